@@ -1,0 +1,204 @@
+"""CPU oracle for fused-sampling influence maximization (arXiv 2008.03095).
+
+TEST INFRASTRUCTURE ONLY: the test suite, the package smoke check and the
+benchmark's CPU-baseline leg are the only users. The product path never
+imports this module. The oracle is a slow, literal C++ restatement of the
+method (Section 3.1 Eq. 1-2, Algorithms 1, 4, 5 and 7 on fixed samples); see
+im_oracle.cpp for the definition of every quantity.
+
+Every function takes and returns numpy arrays (host memory) and raises
+ValueError when the oracle rejects its input.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        i32, i64, u32, u64, f64 = (ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32,
+                                   ctypes.c_uint64, ctypes.c_double)
+        P = ctypes.c_void_p
+        L.orc_murmur3_x86_32.argtypes = [P, i32, u32]
+        L.orc_murmur3_x86_32.restype = u32
+        L.orc_edge_hash.argtypes = [i32, i32]
+        L.orc_edge_hash.restype = u32
+        L.orc_mt19937.argtypes = [u32, i64, P]
+        L.orc_mt19937.restype = None
+        L.orc_threshold.argtypes = [f64]
+        L.orc_threshold.restype = u64
+        L.orc_live.argtypes = [i32, i32, u32, f64]
+        L.orc_live.restype = i32
+        L.orc_validate_csr.argtypes = [i32, i64, P, P]
+        L.orc_validate_csr.restype = i32
+        L.orc_labels.argtypes = [i32, i64, P, P, i32, f64, u32, P, P]
+        L.orc_labels.restype = i32
+        L.orc_labels_lanes.argtypes = [i32, i64, P, P, i32, f64, u32, i32, P, P, P]
+        L.orc_labels_lanes.restype = i32
+        L.orc_select_seeds.argtypes = [i32, i64, P, P, i32, i32, f64, u32, P, P]
+        L.orc_select_seeds.restype = i32
+        L.orc_estimate_spread.argtypes = [i32, i64, P, P, P, i32, i32, f64, u32, P]
+        L.orc_estimate_spread.restype = i32
+        L.orc_greedy_from_tables.argtypes = [i32, i32, P, P, i32, P, P]
+        L.orc_greedy_from_tables.restype = i32
+        L.orc_marginal_gains.argtypes = [i32, i32, P, P, P, i32, P]
+        L.orc_marginal_gains.restype = i32
+        L.orc_labels_masked.argtypes = [i32, i64, P, P, i32, P, P, P]
+        L.orc_labels_masked.restype = i32
+        L.orc_select_seeds_masked.argtypes = [i32, i64, P, P, i32, i32, P, P, P]
+        L.orc_select_seeds_masked.restype = i32
+        L.orc_estimate_spread_masked.argtypes = [i32, i64, P, P, P, i32, i32, P, P]
+        L.orc_estimate_spread_masked.restype = i32
+        _lib = L
+    return _lib
+
+
+def _p(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _csr(xadj, adj):
+    xadj = np.ascontiguousarray(xadj, dtype=np.int32)
+    adj = np.ascontiguousarray(adj, dtype=np.int32)
+    n = xadj.shape[0] - 1
+    m = adj.shape[0] // 2
+    return n, m, xadj, adj
+
+
+def _check(rc, what):
+    if rc != 0:
+        raise ValueError("oracle rejected input to " + what)
+
+
+def murmur3_x86_32(data: bytes, seed: int = 0) -> int:
+    buf = np.frombuffer(bytes(data) + b"\0", dtype=np.uint8)
+    return int(lib().orc_murmur3_x86_32(_p(buf), len(data), seed & 0xFFFFFFFF))
+
+
+def edge_hash(u: int, v: int) -> int:
+    return int(lib().orc_edge_hash(u, v))
+
+
+def mt19937(seed: int, count: int) -> np.ndarray:
+    out = np.empty(count, dtype=np.uint32)
+    lib().orc_mt19937(seed & 0xFFFFFFFF, count, _p(out))
+    return out
+
+
+def threshold(p: float) -> int:
+    return int(lib().orc_threshold(p))
+
+
+def live(u: int, v: int, x: int, p: float) -> bool:
+    return bool(lib().orc_live(u, v, x & 0xFFFFFFFF, p))
+
+
+def validate_csr(xadj, adj) -> bool:
+    n, m, xadj, adj = _csr(xadj, adj)
+    if n < 1 or adj.shape[0] % 2:
+        return False
+    return lib().orc_validate_csr(n, m, _p(xadj), _p(adj)) == 0
+
+
+def labels(xadj, adj, R, p, seed):
+    """(labels, sizes), each n x R (vertex-major), hash sampler."""
+    n, m, xadj, adj = _csr(xadj, adj)
+    lab = np.empty((n, R), dtype=np.int32)
+    siz = np.empty((n, R), dtype=np.uint32)
+    _check(lib().orc_labels(n, m, _p(xadj), _p(adj), R, p, seed, _p(lab), _p(siz)), "labels")
+    return lab, siz
+
+
+def labels_lanes(xadj, adj, R, p, seed, lanes):
+    """(labels, sizes) for the simulations listed in `lanes`: n x len(lanes)."""
+    n, m, xadj, adj = _csr(xadj, adj)
+    lanes = np.ascontiguousarray(lanes, dtype=np.int32)
+    nl = lanes.shape[0]
+    lab = np.empty((n, nl), dtype=np.int32)
+    siz = np.empty((n, nl), dtype=np.uint32)
+    _check(lib().orc_labels_lanes(n, m, _p(xadj), _p(adj), R, p, seed, nl, _p(lanes), _p(lab),
+                                  _p(siz)), "labels_lanes")
+    return lab, siz
+
+
+def select_seeds(xadj, adj, K, R, p, seed):
+    """(seeds int32[K], sigmaR uint64[K]) by greedy over the R fixed samples."""
+    n, m, xadj, adj = _csr(xadj, adj)
+    seeds = np.empty(K, dtype=np.int32)
+    sigma = np.empty(K, dtype=np.uint64)
+    _check(lib().orc_select_seeds(n, m, _p(xadj), _p(adj), K, R, p, seed, _p(seeds), _p(sigma)),
+           "select_seeds")
+    return seeds, sigma
+
+
+def estimate_spread(xadj, adj, seeds, R, p, seed) -> int:
+    n, m, xadj, adj = _csr(xadj, adj)
+    seeds = np.ascontiguousarray(seeds, dtype=np.int32)
+    out = np.zeros(1, dtype=np.uint64)
+    _check(lib().orc_estimate_spread(n, m, _p(xadj), _p(adj), _p(seeds), seeds.shape[0], R, p,
+                                     seed, _p(out)), "estimate_spread")
+    return int(out[0])
+
+
+def greedy_from_tables(lab, siz, K):
+    lab = np.ascontiguousarray(lab, dtype=np.int32)
+    siz = np.ascontiguousarray(siz, dtype=np.uint32)
+    n, R = lab.shape
+    seeds = np.empty(K, dtype=np.int32)
+    sigma = np.empty(K, dtype=np.uint64)
+    _check(lib().orc_greedy_from_tables(n, R, _p(lab), _p(siz), K, _p(seeds), _p(sigma)),
+           "greedy_from_tables")
+    return seeds, sigma
+
+
+def marginal_gains(lab, siz, S):
+    lab = np.ascontiguousarray(lab, dtype=np.int32)
+    siz = np.ascontiguousarray(siz, dtype=np.uint32)
+    S = np.ascontiguousarray(S, dtype=np.int32)
+    n, R = lab.shape
+    g = np.empty(n, dtype=np.uint64)
+    _check(lib().orc_marginal_gains(n, R, _p(lab), _p(siz), _p(S), S.shape[0], _p(g)),
+           "marginal_gains")
+    return g
+
+
+def labels_masked(xadj, adj, mask):
+    """mask: uint8 [2m, R], mask[a, r] = arc a live in sample r (symmetric)."""
+    n, m, xadj, adj = _csr(xadj, adj)
+    mask = np.ascontiguousarray(mask, dtype=np.uint8)
+    R = mask.shape[1]
+    lab = np.empty((n, R), dtype=np.int32)
+    siz = np.empty((n, R), dtype=np.uint32)
+    _check(lib().orc_labels_masked(n, m, _p(xadj), _p(adj), R, _p(mask), _p(lab), _p(siz)),
+           "labels_masked")
+    return lab, siz
+
+
+def select_seeds_masked(xadj, adj, K, mask):
+    n, m, xadj, adj = _csr(xadj, adj)
+    mask = np.ascontiguousarray(mask, dtype=np.uint8)
+    R = mask.shape[1]
+    seeds = np.empty(K, dtype=np.int32)
+    sigma = np.empty(K, dtype=np.uint64)
+    _check(lib().orc_select_seeds_masked(n, m, _p(xadj), _p(adj), K, R, _p(mask), _p(seeds),
+                                         _p(sigma)), "select_seeds_masked")
+    return seeds, sigma
+
+
+def estimate_spread_masked(xadj, adj, seeds, mask) -> int:
+    n, m, xadj, adj = _csr(xadj, adj)
+    mask = np.ascontiguousarray(mask, dtype=np.uint8)
+    seeds = np.ascontiguousarray(seeds, dtype=np.int32)
+    R = mask.shape[1]
+    out = np.zeros(1, dtype=np.uint64)
+    _check(lib().orc_estimate_spread_masked(n, m, _p(xadj), _p(adj), _p(seeds), seeds.shape[0],
+                                            R, _p(mask), _p(out)), "estimate_spread_masked")
+    return int(out[0])
