@@ -1,0 +1,201 @@
+/*
+ * im.h -- C ABI of the GB300 (sm_103a) fused-sampling influence-maximization
+ * library (INFuseR-MG hot path of Goktürk & Kaya, arXiv 2008.03095).
+ *
+ * Problem (Section 2.1): given an undirected graph G = (V, E), a seed-set size
+ * K and R Monte-Carlo simulations under the independent-cascade model with a
+ * uniform edge probability p, choose S (|S| = K) greedily to maximize the
+ * estimated spread sigma(S).
+ *
+ * Sampling (Section 3.1, Eq. 1-2): edge {u,v} is live in simulation r iff
+ *     (uint64)(X_r XOR h(u,v)) < T,   T = floor(p * 2^32)
+ * where h(u,v) = MurmurHash3_x86_32 of the 8-byte key min(u,v) || max(u,v)
+ * (little-endian uint32 halves, seed 0) and X_0..X_{R-1} are the first R
+ * outputs of MT19937 seeded with rng_seed (the std::mt19937 sequence). No
+ * sampled graph is ever stored: every arc is decided when it is read.
+ *
+ * Estimate: sigmaR(S) = sum over r of |vertices reachable from S in sample r|
+ * (an integer; sigma = sigmaR / R). Seeds follow Algorithm 7: component labels
+ * of every sample (Algorithm 5), memoized component sizes (Section 3.3), then
+ * greedy/CELF selection of marginal gains summed over the R samples, ties
+ * broken by the lowest vertex id. out_sigma_R[k] is sigmaR of the first k+1
+ * seeds.
+ *
+ * Conventions
+ *   - Every function returns IM_OK (0) or a negative IM_E* code; on error no
+ *     output is written and im_last_error() describes the failure.
+ *   - Vertex ids are int32 in [0, n). CSR: xadj[n+1], adj[2m], xadj[0] = 0,
+ *     xadj non-decreasing, xadj[n] = 2m, every arc (u,v) has a reverse arc
+ *     (v,u). Self-loops are accepted and ignored; duplicate arcs are accepted.
+ *     Neighbour lists need not be sorted (unsorted lists are sorted once, on
+ *     the host, at graph creation).
+ *   - Limits: 1 <= n < 2^31, 2m < 2^31, 1 <= R <= 65536, n * R < 2^32,
+ *     0 <= K <= n, 0 <= p <= 1 (NaN rejected).
+ *   - "host" pointers are ordinary CPU memory; "device" pointers are CUDA
+ *     global memory of the device the graph was created on.
+ *   - Work is queued on the calling thread's stream (im_set_stream; default:
+ *     the legacy default stream). Blocking calls synchronize that stream.
+ *   - Graph handles are read-only after creation. Blocking calls on one graph
+ *     from several threads are serialized internally; workspaces are not
+ *     thread-safe (one workspace per concurrent query stream).
+ */
+#ifndef IM_GB300_IM_H
+#define IM_GB300_IM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  IM_OK = 0,
+  IM_EINVAL = -1,    /* invalid argument or malformed graph */
+  IM_ENOMEM = -2,    /* device allocation failed; handles stay valid */
+  IM_ECUDA = -3,     /* CUDA runtime error */
+  IM_ETIMEOUT = -4,  /* a device loop exceeded its iteration budget */
+  IM_EBUSY = -5,     /* resource in use */
+  IM_EINTERNAL = -6  /* internal invariant violated */
+};
+
+typedef struct im_graph im_graph;         /* opaque, library-owned */
+typedef struct im_workspace im_workspace; /* opaque, library-owned */
+
+/* ---------------------------------------------------------------- graphs */
+
+/* Validate a symmetric CSR (host arrays, see Conventions) and copy it to the
+ * current device, where it stays resident until im_graph_destroy. The
+ * library also derives the upper-triangle edge list {u < v} used by the
+ * component kernel. Blocking. The caller keeps ownership of xadj/adj.
+ * Errors: IM_EINVAL (bad CSR: ranges, ids, asymmetry), IM_ENOMEM, IM_ECUDA. */
+int im_graph_create(int32_t n, int64_t m, const int32_t *xadj, const int32_t *adj,
+                    im_graph **out);
+
+/* Release a graph and its device memory (and its internal workspace). */
+int im_graph_destroy(im_graph *g);
+
+/* Number of vertices and undirected edges (m = len(adj) / 2). */
+int im_graph_info(const im_graph *g, int32_t *n, int64_t *m);
+
+/* ---------------------------------------------------------------- queries */
+
+/* Select K seeds (Algorithm 7, INFuseR-MG): fused sampling + component labels
+ * of all R samples, memoized sizes, first-seed gains mg_v = sum_r |C_r(v)|,
+ * then exact CELF. out_seeds[K] and out_sigma_R[K] are host arrays owned by
+ * the caller; out_sigma_R[k] = sigmaR({s_0..s_k}). Blocking.
+ * Errors: IM_EINVAL (K, R, p out of range), IM_ENOMEM, IM_ECUDA, IM_ETIMEOUT. */
+int im_select_seeds(const im_graph *g, int32_t K, int32_t R, double p, uint32_t rng_seed,
+                    int32_t *out_seeds, uint64_t *out_sigma_R);
+
+/* Spread of a given seed set (Algorithm 4 evaluated on the same fixed hash
+ * samples, Eq. 2): *out_sigma_R = sum_r |union_{s in S} C_r(s)|. seeds is a
+ * host array of num_seeds ids; duplicates count once. Blocking. */
+int im_estimate_spread(const im_graph *g, const int32_t *seeds, int32_t num_seeds, int32_t R,
+                       double p, uint32_t rng_seed, uint64_t *out_sigma_R);
+
+/* ---------------------------------------------------------------- async API */
+
+/* Device scratch for queries with R <= R_max on graph g (about
+ * n*R*4 + n*R/8 + 8n bytes). Owned by the library until destroyed. */
+int im_workspace_create(const im_graph *g, int32_t R_max, im_workspace **out);
+int im_workspace_destroy(im_workspace *ws);
+
+/* Same as im_select_seeds, queued on the thread's stream without
+ * synchronizing: d_seeds[K] (int32) and d_sigma_R[K] (uint64) are DEVICE
+ * arrays owned by the caller. Device-side failures are recorded in the
+ * workspace and reported by im_workspace_status. */
+int im_select_seeds_async(const im_graph *g, im_workspace *ws, int32_t K, int32_t R, double p,
+                          uint32_t rng_seed, int32_t *d_seeds, uint64_t *d_sigma_R);
+
+/* Same as im_estimate_spread with DEVICE d_seeds[num_seeds] and DEVICE
+ * d_sigma_R[1]; queued without synchronizing. Seed ids are checked on the
+ * device (an out-of-range id sets IM_EINVAL in the workspace status). */
+int im_estimate_spread_async(const im_graph *g, im_workspace *ws, const int32_t *d_seeds,
+                             int32_t num_seeds, int32_t R, double p, uint32_t rng_seed,
+                             uint64_t *d_sigma_R);
+
+/* Synchronize the thread's stream and return (then clear) the first device
+ * status recorded in ws since the last call: IM_OK, IM_EINVAL, IM_ETIMEOUT or
+ * IM_EINTERNAL. */
+int im_workspace_status(im_workspace *ws);
+
+/* ---------------------------------------------------------------- misc */
+
+/* Thread-local description of the last failure of this thread (valid until
+ * the thread's next library call). Never NULL. */
+const char *im_last_error(void);
+
+/* Set the calling thread's CUDA stream (a cudaStream_t, e.g.
+ * torch.cuda.current_stream().cuda_stream); NULL selects the legacy default
+ * stream. */
+int im_set_stream(void *cuda_stream);
+
+/* Host-only helper: the sampling threshold T = floor(p * 2^32) of Eq. 2 for
+ * p in [0, 1]; returns IM_EINVAL for p outside [0, 1] or NaN. */
+int im_sampling_threshold(double p, uint64_t *out_T);
+
+/* ---------------------------------------------------------------- profiling
+ * Optional per-phase timing of the calling thread's queries: when enabled,
+ * every kernel the library launches is bracketed by CUDA events recorded on
+ * the same stream. Phases: */
+enum {
+  IM_PHASE_PREP = 0,         /* X_r draw, lane order, label-table init */
+  IM_PHASE_UNION = 1,        /* fused hash-sample + component hooking */
+  IM_PHASE_COMPRESS = 2,     /* root pointers + size memo */
+  IM_PHASE_GAINS = 3,        /* first-seed gains mg_v */
+  IM_PHASE_CELF = 4,         /* on-device lazy greedy */
+  IM_PHASE_SPREAD_PREP = 5,  /* X_r draw and lane order for the spread */
+  IM_PHASE_SPREAD = 6,       /* bit-parallel multi-source BFS */
+  IM_NUM_PHASES = 7
+};
+
+/* on != 0 starts recording (and clears earlier records); 0 stops. */
+int im_profile_enable(int on);
+
+/* Synchronize the recorded events and return, per phase, the summed kernel
+ * time in milliseconds and the number of launches since the last enable or
+ * read (host arrays of IM_NUM_PHASES entries, either may be NULL); clears the
+ * records. */
+int im_profile_read(double *total_ms, int64_t *launches);
+
+/* Number of kernels this library has launched in this process (all threads). */
+uint64_t im_kernel_launches(void);
+
+/* ---------------------------------------------------------------- test hooks
+ * Test-only exports used to compare intermediate tables with the oracle. All
+ * outputs are host arrays owned by the caller; all calls are blocking. */
+
+/* Component labels of all R samples in the paper's layout: out[v*R + r] is
+ * the minimum vertex id of v's component in sample r (Algorithm 5 fixpoint). */
+int im_debug_labels(const im_graph *g, int32_t R, double p, uint32_t rng_seed,
+                    int32_t *out_labels);
+
+/* Size memo (Section 3.3): out[l*R + r] = #{v : label of v in sample r is l},
+ * zero where l is not a component label of sample r. */
+int im_debug_sizes(const im_graph *g, int32_t R, double p, uint32_t rng_seed,
+                   uint32_t *out_sizes);
+
+/* The per-simulation random values X_0..X_{R-1} as drawn on the device. */
+int im_debug_lane_randoms(int32_t R, uint32_t rng_seed, uint32_t *out_X);
+
+/* Edge hashes h(u[i], v[i]) (Eq. 1) computed by the device hash routine. */
+int im_debug_edge_hash(const int32_t *u, const int32_t *v, int64_t count, uint32_t *out_h);
+
+/* Seed selection with an explicit live mask instead of the hash sampler:
+ * mask[a*R + r] != 0 iff CSR arc a is live in sample r (both orientations of
+ * an edge must agree). out_labels[n*R] / out_sizes[n*R] may be NULL. Used to
+ * feed the worked example of Figures 3-4 and brute-force enumerations. */
+int im_debug_select_seeds_masked(const im_graph *g, int32_t K, int32_t R, const uint8_t *mask,
+                                 int32_t *out_seeds, uint64_t *out_sigma_R,
+                                 int32_t *out_labels, uint32_t *out_sizes);
+
+/* Spread with an explicit live mask (same layout as above). */
+int im_debug_estimate_spread_masked(const im_graph *g, const int32_t *seeds, int32_t num_seeds,
+                                    int32_t R, const uint8_t *mask, uint64_t *out_sigma_R);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IM_GB300_IM_H */

@@ -1,0 +1,16 @@
+"""GB300 (sm_103a) fused-sampling influence maximization (INFuseR-MG hot path,
+arXiv 2008.03095) behind a small C ABI (include/im.h).
+
+The Python names mirror the C entry points; all computation runs in the CUDA
+library built by `paper_2008_03095_gb300.build.build()`.
+"""
+from ._binding import (IM_EBUSY, IM_ECUDA, IM_EINTERNAL, IM_EINVAL, IM_ENOMEM, IM_ETIMEOUT,
+                       IM_OK, Graph, IMError, Workspace, header_functions,
+                       im_debug_edge_hash, im_debug_estimate_spread_masked, im_debug_labels,
+                       im_debug_lane_randoms, im_debug_select_seeds_masked, im_debug_sizes,
+                       im_estimate_spread, im_estimate_spread_async, im_graph_create,
+                       im_graph_create_raw, im_graph_destroy, im_graph_info, im_kernel_launches,
+                       im_last_error, im_profile_enable, im_profile_read, PHASES,
+                       im_sampling_threshold, im_select_seeds, im_select_seeds_async,
+                       im_set_stream, im_workspace_create, im_workspace_destroy,
+                       im_workspace_status, lib, library_path)

@@ -1,0 +1,307 @@
+"""ctypes binding of the C ABI in include/im.h (argument marshalling only).
+
+Every function here keeps the C name and forwards to the sm_103a library
+paper_2008_03095_gb300/_build/libim_gb300.so; there is no CPU fallback. If
+the library has not been built, the first call raises RuntimeError.
+Host arrays are numpy arrays; device arrays are torch CUDA tensors (or raw
+integer device addresses).
+"""
+import ctypes
+import os
+import re
+
+import numpy as np
+
+from . import build as _build
+
+IM_OK = 0
+IM_EINVAL = -1
+IM_ENOMEM = -2
+IM_ECUDA = -3
+IM_ETIMEOUT = -4
+IM_EBUSY = -5
+IM_EINTERNAL = -6
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include",
+                      "im.h")
+
+
+class IMError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("im error %d: %s" % (code, msg))
+        self.code = code
+
+
+_lib = None
+
+
+def library_path():
+    return _build.LIB
+
+
+def lib():
+    """Load the CUDA library (raises if it was not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError("CUDA library %s is missing: build it with "
+                           "paper_2008_03095_gb300.build.build(); there is no CPU fallback" % path)
+    L = ctypes.CDLL(path)
+    i32, i64, u32, u64, f64, P = (ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32,
+                                  ctypes.c_uint64, ctypes.c_double, ctypes.c_void_p)
+    sig = {
+        "im_graph_create": [i32, i64, P, P, P],
+        "im_graph_destroy": [P],
+        "im_graph_info": [P, P, P],
+        "im_select_seeds": [P, i32, i32, f64, u32, P, P],
+        "im_estimate_spread": [P, P, i32, i32, f64, u32, P],
+        "im_workspace_create": [P, i32, P],
+        "im_workspace_destroy": [P],
+        "im_select_seeds_async": [P, P, i32, i32, f64, u32, P, P],
+        "im_estimate_spread_async": [P, P, P, i32, i32, f64, u32, P],
+        "im_workspace_status": [P],
+        "im_set_stream": [P],
+        "im_sampling_threshold": [f64, P],
+        "im_debug_labels": [P, i32, f64, u32, P],
+        "im_debug_sizes": [P, i32, f64, u32, P],
+        "im_debug_lane_randoms": [i32, u32, P],
+        "im_debug_edge_hash": [P, P, i64, P],
+        "im_debug_select_seeds_masked": [P, i32, i32, P, P, P, P, P],
+        "im_debug_estimate_spread_masked": [P, P, i32, i32, P, P],
+        "im_profile_enable": [ctypes.c_int],
+        "im_profile_read": [P, P],
+    }
+    for name, args in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    L.im_last_error.argtypes = []
+    L.im_last_error.restype = ctypes.c_char_p
+    L.im_kernel_launches.argtypes = []
+    L.im_kernel_launches.restype = ctypes.c_uint64
+    _lib = L
+    return L
+
+
+def header_functions():
+    """Names of every function declared in include/im.h."""
+    with open(HEADER) as f:
+        text = f.read()
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(im_\w+)\s*\(", text, re.M)))
+
+
+def im_last_error():
+    return lib().im_last_error().decode()
+
+
+def _check(rc):
+    if rc != IM_OK:
+        raise IMError(rc, im_last_error())
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if isinstance(a, int):
+        return ctypes.c_void_p(a)
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data_as(ctypes.c_void_p)
+    if hasattr(a, "data_ptr"):
+        return ctypes.c_void_p(a.data_ptr())
+    raise TypeError("unsupported array type %r" % type(a))
+
+
+class Graph:
+    """Owning wrapper of an im_graph handle."""
+
+    def __init__(self, handle, n, m):
+        self.handle = handle
+        self.n = n
+        self.m = m
+
+    def close(self):
+        if self.handle:
+            _check(lib().im_graph_destroy(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Workspace:
+    """Owning wrapper of an im_workspace handle."""
+
+    def __init__(self, handle, graph, R_max):
+        self.handle = handle
+        self.graph = graph
+        self.R_max = R_max
+
+    def close(self):
+        if self.handle:
+            _check(lib().im_workspace_destroy(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _gh(g):
+    return g.handle if isinstance(g, Graph) else g
+
+
+def im_graph_create(xadj, adj):
+    xadj = np.ascontiguousarray(xadj, dtype=np.int32)
+    adj = np.ascontiguousarray(adj, dtype=np.int32)
+    n = xadj.shape[0] - 1
+    m = adj.shape[0] // 2
+    out = ctypes.c_void_p()
+    _check(lib().im_graph_create(n, m, _ptr(xadj), _ptr(adj) if adj.size else None,
+                                 ctypes.byref(out)))
+    return Graph(out, n, m)
+
+
+def im_graph_create_raw(n, m, xadj_ptr, adj_ptr):
+    """Create from raw host addresses (e.g. pinned torch tensors)."""
+    out = ctypes.c_void_p()
+    _check(lib().im_graph_create(n, m, _ptr(xadj_ptr), _ptr(adj_ptr), ctypes.byref(out)))
+    return Graph(out, n, m)
+
+
+def im_graph_destroy(g):
+    g.close()
+
+
+def im_graph_info(g):
+    n = ctypes.c_int32()
+    m = ctypes.c_int64()
+    _check(lib().im_graph_info(_gh(g), ctypes.byref(n), ctypes.byref(m)))
+    return n.value, m.value
+
+
+def im_select_seeds(g, K, R, p, rng_seed, out_seeds=None, out_sigma=None):
+    seeds = np.empty(K, dtype=np.int32) if out_seeds is None else out_seeds
+    sigma = np.empty(K, dtype=np.uint64) if out_sigma is None else out_sigma
+    _check(lib().im_select_seeds(_gh(g), K, R, p, rng_seed & 0xFFFFFFFF, _ptr(seeds), _ptr(sigma)))
+    return seeds, sigma
+
+
+def im_estimate_spread(g, seeds, R, p, rng_seed):
+    seeds = np.ascontiguousarray(seeds, dtype=np.int32)
+    out = ctypes.c_uint64()
+    _check(lib().im_estimate_spread(_gh(g), _ptr(seeds), seeds.shape[0], R, p,
+                                    rng_seed & 0xFFFFFFFF, ctypes.byref(out)))
+    return int(out.value)
+
+
+def im_workspace_create(g, R_max):
+    out = ctypes.c_void_p()
+    _check(lib().im_workspace_create(_gh(g), R_max, ctypes.byref(out)))
+    return Workspace(out, g, R_max)
+
+
+def im_workspace_destroy(ws):
+    ws.close()
+
+
+def im_select_seeds_async(g, ws, K, R, p, rng_seed, d_seeds, d_sigma):
+    _check(lib().im_select_seeds_async(_gh(g), ws.handle, K, R, p, rng_seed & 0xFFFFFFFF,
+                                       _ptr(d_seeds), _ptr(d_sigma)))
+
+
+def im_estimate_spread_async(g, ws, d_seeds, num_seeds, R, p, rng_seed, d_sigma):
+    _check(lib().im_estimate_spread_async(_gh(g), ws.handle, _ptr(d_seeds), num_seeds, R, p,
+                                          rng_seed & 0xFFFFFFFF, _ptr(d_sigma)))
+
+
+def im_workspace_status(ws):
+    _check(lib().im_workspace_status(ws.handle))
+
+
+def im_set_stream(stream):
+    """stream: a torch.cuda.Stream, a raw cudaStream_t integer, or None."""
+    if stream is not None and hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    _check(lib().im_set_stream(ctypes.c_void_p(stream) if stream else None))
+
+
+def im_sampling_threshold(p):
+    out = ctypes.c_uint64()
+    _check(lib().im_sampling_threshold(p, ctypes.byref(out)))
+    return int(out.value)
+
+
+PHASES = ("prep", "union", "compress", "gains", "celf", "spread_prep", "spread")
+
+
+def im_profile_enable(on=True):
+    _check(lib().im_profile_enable(1 if on else 0))
+
+
+def im_profile_read():
+    """{phase: (total_ms, launches)} since the last enable/read."""
+    ms = np.zeros(len(PHASES), dtype=np.float64)
+    cnt = np.zeros(len(PHASES), dtype=np.int64)
+    _check(lib().im_profile_read(_ptr(ms), _ptr(cnt)))
+    return {name: (float(ms[i]), int(cnt[i])) for i, name in enumerate(PHASES)}
+
+
+def im_kernel_launches():
+    return int(lib().im_kernel_launches())
+
+
+# ------------------------------------------------------------------ test hooks
+
+
+def im_debug_labels(g, R, p, rng_seed):
+    out = np.empty((g.n, R), dtype=np.int32)
+    _check(lib().im_debug_labels(_gh(g), R, p, rng_seed & 0xFFFFFFFF, _ptr(out)))
+    return out
+
+
+def im_debug_sizes(g, R, p, rng_seed):
+    out = np.empty((g.n, R), dtype=np.uint32)
+    _check(lib().im_debug_sizes(_gh(g), R, p, rng_seed & 0xFFFFFFFF, _ptr(out)))
+    return out
+
+
+def im_debug_lane_randoms(R, rng_seed):
+    out = np.empty(R, dtype=np.uint32)
+    _check(lib().im_debug_lane_randoms(R, rng_seed & 0xFFFFFFFF, _ptr(out)))
+    return out
+
+
+def im_debug_edge_hash(u, v):
+    u = np.ascontiguousarray(u, dtype=np.int32)
+    v = np.ascontiguousarray(v, dtype=np.int32)
+    out = np.empty(u.shape[0], dtype=np.uint32)
+    _check(lib().im_debug_edge_hash(_ptr(u), _ptr(v), u.shape[0], _ptr(out)))
+    return out
+
+
+def im_debug_select_seeds_masked(g, K, mask, tables=False):
+    mask = np.ascontiguousarray(mask, dtype=np.uint8)
+    R = mask.shape[1]
+    seeds = np.empty(K, dtype=np.int32)
+    sigma = np.empty(K, dtype=np.uint64)
+    lab = np.empty((g.n, R), dtype=np.int32) if tables else None
+    siz = np.empty((g.n, R), dtype=np.uint32) if tables else None
+    _check(lib().im_debug_select_seeds_masked(_gh(g), K, R, _ptr(mask), _ptr(seeds), _ptr(sigma),
+                                              _ptr(lab), _ptr(siz)))
+    return (seeds, sigma, lab, siz) if tables else (seeds, sigma)
+
+
+def im_debug_estimate_spread_masked(g, seeds, mask):
+    mask = np.ascontiguousarray(mask, dtype=np.uint8)
+    seeds = np.ascontiguousarray(seeds, dtype=np.int32)
+    out = ctypes.c_uint64()
+    _check(lib().im_debug_estimate_spread_masked(_gh(g), _ptr(seeds), seeds.shape[0],
+                                                 mask.shape[1], _ptr(mask), ctypes.byref(out)))
+    return int(out.value)

@@ -1,0 +1,670 @@
+// C ABI of the library (declared in include/im.h): argument validation,
+// workspaces, stream handling and the kernel sequence of each query.
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "im_common.cuh"
+
+using namespace imgb;
+
+namespace {
+
+thread_local std::string t_err;
+thread_local cudaStream_t t_stream = nullptr;
+
+// ---- launch accounting and optional per-phase event timing
+std::atomic<uint64_t> g_launches{0};
+struct ProfRec {
+  int phase;
+  cudaEvent_t a, b;
+};
+thread_local bool t_prof_on = false;
+thread_local std::vector<ProfRec> t_recs;
+thread_local std::vector<cudaEvent_t> t_event_pool;
+
+cudaEvent_t prof_event() {
+  if (!t_event_pool.empty()) {
+    cudaEvent_t e = t_event_pool.back();
+    t_event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+// Launch one kernel (through `launch`) for `phase`, bracketed by events on
+// stream s when profiling is on.
+template <class F>
+cudaError_t timed(int phase, cudaStream_t s, F launch) {
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (t_prof_on) {
+    a = prof_event();
+    b = prof_event();
+    if (a) cudaEventRecord(a, s);
+  }
+  cudaError_t e = launch();
+  if (e == cudaSuccess) g_launches.fetch_add(1, std::memory_order_relaxed);
+  if (t_prof_on && a && b) {
+    cudaEventRecord(b, s);
+    t_recs.push_back({phase, a, b});
+  }
+  return e;
+}
+
+int fail(int code, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  std::vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  t_err = buf;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what) {
+  cudaGetLastError();  // clear a non-sticky error
+  return fail(e == cudaErrorMemoryAllocation ? IM_ENOMEM : IM_ECUDA, "%s: %s", what,
+              cudaGetErrorString(e));
+}
+
+#define API_CUDA(expr, what)                         \
+  do {                                               \
+    cudaError_t e_ = (expr);                         \
+    if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+  } while (0)
+
+// Makes the graph's device current for the duration of a call.
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = true;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) {
+      ok = false;
+      return;
+    }
+    if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+int make_params(const im_graph *g, int32_t R, double p, uint32_t seed, QueryParams *q) {
+  if (R < 1 || R > kMaxR) return fail(IM_EINVAL, "R=%d outside [1, %d]", R, kMaxR);
+  if (!(p >= 0.0 && p <= 1.0)) return fail(IM_EINVAL, "p outside [0, 1] or NaN");
+  if (g && (uint64_t)g->n * (uint64_t)R >= (1ull << 32))
+    return fail(IM_EINVAL, "n*R = %llu must be below 2^32",
+                (unsigned long long)((uint64_t)g->n * (uint64_t)R));
+  q->R = (uint32_t)R;
+  q->seed = seed;
+  q->T = (uint64_t)std::floor(p * 4294967296.0);
+  q->all_live = q->T == (1ull << 32);
+  q->none_live = q->T == 0;
+  q->T32 = q->all_live ? 0u : (uint32_t)q->T;
+  int nb = 0;
+  if (!q->all_live && !q->none_live) {
+    const uint64_t t1 = q->T - 1;  // live values are <= T-1 < 2^s
+    const int s = t1 ? 64 - __builtin_clzll(t1) : 0;
+    nb = 32 - s;
+    if (nb > kMaxBucketBits) nb = kMaxBucketBits;
+  }
+  q->nb = nb;
+  return IM_OK;
+}
+
+template <class T>
+cudaError_t dalloc(T **p, size_t count) {
+  return cudaMalloc(reinterpret_cast<void **>(p), sizeof(T) * (count ? count : 1));
+}
+
+void ws_free(im_workspace *ws) {
+  void *ptrs[] = {ws->d_P,    ws->d_cov,  ws->d_keys, ws->d_keyrange, ws->d_pool,
+                  ws->d_X,    ws->d_Xs,   ws->d_perm, ws->d_boff,     ws->d_sortbuf,
+                  ws->d_V,    ws->d_F0,   ws->d_F1,   ws->d_L0,       ws->d_L1,
+                  ws->d_inlist, ws->d_cnt, ws->d_acc, ws->d_status,   ws->d_seeds_out,
+                  ws->d_sigma_out, ws->d_seeds_in, ws->d_mask};
+  for (void *p : ptrs)
+    if (p) cudaFree(p);
+}
+
+int ws_create(const im_graph *g, int32_t R_max, im_workspace **out) {
+  im_workspace *ws = new (std::nothrow) im_workspace();
+  if (!ws) return fail(IM_ENOMEM, "host allocation failed");
+  ws->g = g;
+  ws->device = g->device;
+  ws->R_max = R_max;
+  const size_t n = (size_t)g->n;
+  const size_t nR = n * (size_t)R_max;
+  const size_t W = ((size_t)R_max + 31) / 32;
+  cudaError_t e = cudaSuccess;
+  size_t npow2 = 1;
+  while (npow2 < (size_t)R_max) npow2 <<= 1;
+#define WS_ALLOC(ptr, cnt)                 \
+  if (e == cudaSuccess) e = dalloc(&ws->ptr, (cnt));
+  WS_ALLOC(d_P, nR);
+  WS_ALLOC(d_cov, (nR + 31) / 32);
+  WS_ALLOC(d_keys, n);
+  WS_ALLOC(d_keyrange, 2);
+  WS_ALLOC(d_pool, (size_t)R_max * 8 > (size_t)160 * 1024 ? (size_t)2 * 8 * R_max : 1);
+  WS_ALLOC(d_X, R_max);
+  WS_ALLOC(d_Xs, R_max);
+  WS_ALLOC(d_perm, R_max);
+  WS_ALLOC(d_boff, (1u << kMaxBucketBits) + 1);
+  WS_ALLOC(d_sortbuf, npow2 > (size_t)kSortSmemMax ? npow2 : 1);
+  WS_ALLOC(d_V, n * W);
+  WS_ALLOC(d_F0, n * W);
+  WS_ALLOC(d_F1, n * W);
+  WS_ALLOC(d_L0, n);
+  WS_ALLOC(d_L1, n);
+  WS_ALLOC(d_inlist, n);
+  WS_ALLOC(d_cnt, 4);
+  WS_ALLOC(d_acc, 1);
+  WS_ALLOC(d_status, 1);
+  WS_ALLOC(d_seeds_out, n);
+  WS_ALLOC(d_sigma_out, n);
+#undef WS_ALLOC
+  if (e == cudaSuccess) e = cudaMemset(ws->d_status, 0, sizeof(int32_t));
+  if (e != cudaSuccess) {
+    ws_free(ws);
+    delete ws;
+    return cuda_fail(e, "workspace allocation");
+  }
+  *out = ws;
+  return IM_OK;
+}
+
+int check_ws(const im_graph *g, const im_workspace *ws, int32_t R) {
+  if (!g || !ws) return fail(IM_EINVAL, "null graph or workspace");
+  if (ws->g != g) return fail(IM_EINVAL, "workspace belongs to another graph");
+  if (R > ws->R_max) return fail(IM_EINVAL, "R=%d exceeds the workspace's R_max=%d", R, ws->R_max);
+  return IM_OK;
+}
+
+// The kernel sequence of one select query (Algorithm 7).
+int enqueue_select(const im_graph *g, const im_workspace *ws, int32_t K, const QueryParams &q,
+                   const uint8_t *d_mask, int32_t *d_seeds, uint64_t *d_sigma, cudaStream_t s,
+                   bool stop_after_tables) {
+  QueryParams qq = q;
+  if (d_mask) {  // explicit live mask: identity lane order, every lane a candidate
+    qq.nb = 0;
+    qq.none_live = 0;
+  }
+  API_CUDA(timed(IM_PHASE_PREP, s, [&] { return launch_prep(ws, qq, true, !stop_after_tables, s); }),
+           "k_prep");
+  if (!qq.none_live && g->m_up > 0) {
+    API_CUDA(timed(IM_PHASE_UNION, s, [&] { return launch_union(g, ws, qq, d_mask, s); }),
+             "k_union");
+    API_CUDA(timed(IM_PHASE_COMPRESS, s, [&] { return launch_compress(g, ws, qq, s); }),
+             "k_compress");
+  }
+  if (stop_after_tables) return IM_OK;
+  API_CUDA(timed(IM_PHASE_GAINS, s, [&] { return launch_gains(g, ws, qq, s); }), "k_gains");
+  API_CUDA(timed(IM_PHASE_CELF, s,
+                 [&] { return launch_celf(g, ws, qq, K, d_seeds, d_sigma, s); }),
+           "k_celf");
+  return IM_OK;
+}
+
+int enqueue_spread(const im_graph *g, const im_workspace *ws, const int32_t *d_seeds, int32_t ns,
+                   const QueryParams &q, const uint8_t *d_mask, uint64_t *d_sigma, cudaStream_t s) {
+  QueryParams qq = q;
+  if (d_mask) qq.nb = 0;
+  API_CUDA(timed(IM_PHASE_SPREAD_PREP, s, [&] { return launch_prep(ws, qq, false, false, s); }),
+           "k_prep");
+  API_CUDA(timed(IM_PHASE_SPREAD, s,
+                 [&] { return launch_spread(g, ws, qq, d_seeds, ns, d_mask, d_sigma, s); }),
+           "k_spread");
+  return IM_OK;
+}
+
+// Status word: read, clear, translate.
+int take_status(const im_workspace *ws, cudaStream_t s) {
+  int32_t st = 0;
+  API_CUDA(cudaMemcpyAsync(&st, ws->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, s),
+           "status copy");
+  API_CUDA(cudaStreamSynchronize(s), "stream synchronize");
+  if (st != 0) {
+    API_CUDA(cudaMemsetAsync(ws->d_status, 0, sizeof(int32_t), s), "status clear");
+    API_CUDA(cudaStreamSynchronize(s), "stream synchronize");
+    const char *what = st == IM_ETIMEOUT ? "a device loop exceeded its iteration budget"
+                       : st == IM_EINVAL ? "invalid seed id"
+                                         : "device-side invariant violated";
+    return fail(st, "%s", what);
+  }
+  return IM_OK;
+}
+
+// Internal workspace of a graph for blocking calls (grown on demand).
+int internal_ws(im_graph *g, int32_t R, im_workspace **out) {
+  if (g->ws && g->ws->R_max >= R) {
+    *out = g->ws;
+    return IM_OK;
+  }
+  if (g->ws) {
+    ws_free(g->ws);
+    delete g->ws;
+    g->ws = nullptr;
+  }
+  int rc = ws_create(g, R, &g->ws);
+  if (rc != IM_OK) return rc;
+  *out = g->ws;
+  return IM_OK;
+}
+
+int ensure_mask(im_workspace *ws, size_t bytes) {
+  if (ws->mask_cap >= bytes) return IM_OK;
+  if (ws->d_mask) cudaFree(ws->d_mask);
+  ws->d_mask = nullptr;
+  ws->mask_cap = 0;
+  API_CUDA(cudaMalloc(&ws->d_mask, bytes ? bytes : 1), "cudaMalloc mask");
+  ws->mask_cap = bytes;
+  return IM_OK;
+}
+
+int ensure_seed_in(im_workspace *ws, int64_t count) {
+  if (ws->seed_in_cap >= count && ws->d_seeds_in) return IM_OK;
+  if (ws->d_seeds_in) cudaFree(ws->d_seeds_in);
+  ws->d_seeds_in = nullptr;
+  ws->seed_in_cap = 0;
+  API_CUDA(dalloc(&ws->d_seeds_in, (size_t)(count > 0 ? count : 1)), "cudaMalloc seeds");
+  ws->seed_in_cap = count > 0 ? count : 1;
+  return IM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *im_last_error(void) { return t_err.c_str(); }
+
+int im_set_stream(void *cuda_stream) {
+  t_stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+  return IM_OK;
+}
+
+int im_profile_enable(int on) {
+  for (auto &r : t_recs) {
+    t_event_pool.push_back(r.a);
+    t_event_pool.push_back(r.b);
+  }
+  t_recs.clear();
+  t_prof_on = on != 0;
+  return IM_OK;
+}
+
+int im_profile_read(double *total_ms, int64_t *launches) {
+  double ms[IM_NUM_PHASES] = {0};
+  int64_t cnt[IM_NUM_PHASES] = {0};
+  int rc = IM_OK;
+  for (auto &r : t_recs) {
+    float t = 0.f;
+    cudaError_t e = cudaEventSynchronize(r.b);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, r.a, r.b);
+    if (e != cudaSuccess && rc == IM_OK) rc = cuda_fail(e, "profile events");
+    if (r.phase >= 0 && r.phase < IM_NUM_PHASES) {
+      ms[r.phase] += t;
+      cnt[r.phase] += 1;
+    }
+    t_event_pool.push_back(r.a);
+    t_event_pool.push_back(r.b);
+  }
+  t_recs.clear();
+  for (int i = 0; i < IM_NUM_PHASES; ++i) {
+    if (total_ms) total_ms[i] = ms[i];
+    if (launches) launches[i] = cnt[i];
+  }
+  return rc;
+}
+
+uint64_t im_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+int im_sampling_threshold(double p, uint64_t *out_T) {
+  if (!out_T) return fail(IM_EINVAL, "null output");
+  QueryParams q;
+  int rc = make_params(nullptr, 1, p, 0, &q);
+  if (rc != IM_OK) return rc;
+  *out_T = q.T;
+  return IM_OK;
+}
+
+int im_graph_create(int32_t n, int64_t m, const int32_t *xadj, const int32_t *adj,
+                    im_graph **out) {
+  if (!out) return fail(IM_EINVAL, "null output handle");
+  if (n < 1) return fail(IM_EINVAL, "n=%d must be >= 1", n);
+  if (m < 0) return fail(IM_EINVAL, "m must be >= 0");
+  if (2 * m >= (1ll << 31)) return fail(IM_EINVAL, "2m must be below 2^31");
+  if (!xadj || (m > 0 && !adj)) return fail(IM_EINVAL, "null CSR array");
+  if (xadj[0] != 0) return fail(IM_EINVAL, "xadj[0] must be 0");
+  if ((int64_t)xadj[n] != 2 * m) return fail(IM_EINVAL, "xadj[n] must equal 2m");
+  im_graph *g = new (std::nothrow) im_graph();
+  if (!g) return fail(IM_ENOMEM, "host allocation failed");
+  g->n = n;
+  g->m = m;
+  cudaError_t e = cudaGetDevice(&g->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device);
+  if (e != cudaSuccess) {
+    delete g;
+    return cuda_fail(e, "device query");
+  }
+  char err[256] = {0};
+  int rc = graph_build_device(g, xadj, adj, err, sizeof(err));
+  if (rc != IM_OK) {
+    if (g->d_xadj) cudaFree(g->d_xadj);
+    if (g->d_adj) cudaFree(g->d_adj);
+    if (g->d_eu) cudaFree(g->d_eu);
+    if (g->d_ev) cudaFree(g->d_ev);
+    delete g;
+    return fail(rc, "%s", err);
+  }
+  *out = g;
+  return IM_OK;
+}
+
+int im_graph_destroy(im_graph *g) {
+  if (!g) return fail(IM_EINVAL, "null graph");
+  DeviceGuard dg(g->device);
+  if (g->ws) {
+    ws_free(g->ws);
+    delete g->ws;
+  }
+  if (g->d_xadj) cudaFree(g->d_xadj);
+  if (g->d_adj) cudaFree(g->d_adj);
+  if (g->d_eu) cudaFree(g->d_eu);
+  if (g->d_ev) cudaFree(g->d_ev);
+  delete g;
+  return IM_OK;
+}
+
+int im_graph_info(const im_graph *g, int32_t *n, int64_t *m) {
+  if (!g) return fail(IM_EINVAL, "null graph");
+  if (n) *n = g->n;
+  if (m) *m = g->m;
+  return IM_OK;
+}
+
+int im_workspace_create(const im_graph *g, int32_t R_max, im_workspace **out) {
+  if (!g || !out) return fail(IM_EINVAL, "null argument");
+  QueryParams q;
+  int rc = make_params(g, R_max, 0.5, 0, &q);
+  if (rc != IM_OK) return rc;
+  DeviceGuard dg(g->device);
+  if (!dg.ok) return fail(IM_ECUDA, "cannot select the graph's device");
+  return ws_create(g, R_max, out);
+}
+
+int im_workspace_destroy(im_workspace *ws) {
+  if (!ws) return fail(IM_EINVAL, "null workspace");
+  DeviceGuard dg(ws->device);
+  ws_free(ws);
+  delete ws;
+  return IM_OK;
+}
+
+int im_workspace_status(im_workspace *ws) {
+  if (!ws) return fail(IM_EINVAL, "null workspace");
+  DeviceGuard dg(ws->device);
+  return take_status(ws, t_stream);
+}
+
+int im_select_seeds_async(const im_graph *g, im_workspace *ws, int32_t K, int32_t R, double p,
+                          uint32_t rng_seed, int32_t *d_seeds, uint64_t *d_sigma_R) {
+  int rc = check_ws(g, ws, R);
+  if (rc != IM_OK) return rc;
+  if (K < 0 || K > g->n) return fail(IM_EINVAL, "K=%d outside [0, n=%d]", K, g->n);
+  if (K > 0 && (!d_seeds || !d_sigma_R)) return fail(IM_EINVAL, "null output");
+  QueryParams q;
+  rc = make_params(g, R, p, rng_seed, &q);
+  if (rc != IM_OK) return rc;
+  if (K == 0) return IM_OK;
+  DeviceGuard dg(g->device);
+  return enqueue_select(g, ws, K, q, nullptr, d_seeds, d_sigma_R, t_stream, false);
+}
+
+int im_estimate_spread_async(const im_graph *g, im_workspace *ws, const int32_t *d_seeds,
+                             int32_t num_seeds, int32_t R, double p, uint32_t rng_seed,
+                             uint64_t *d_sigma_R) {
+  int rc = check_ws(g, ws, R);
+  if (rc != IM_OK) return rc;
+  if (num_seeds < 0) return fail(IM_EINVAL, "num_seeds < 0");
+  if (!d_sigma_R || (num_seeds > 0 && !d_seeds)) return fail(IM_EINVAL, "null argument");
+  QueryParams q;
+  rc = make_params(g, R, p, rng_seed, &q);
+  if (rc != IM_OK) return rc;
+  DeviceGuard dg(g->device);
+  return enqueue_spread(g, ws, d_seeds, num_seeds, q, nullptr, d_sigma_R, t_stream);
+}
+
+int im_select_seeds(const im_graph *g_, int32_t K, int32_t R, double p, uint32_t rng_seed,
+                    int32_t *out_seeds, uint64_t *out_sigma_R) {
+  if (!g_) return fail(IM_EINVAL, "null graph");
+  im_graph *g = const_cast<im_graph *>(g_);
+  if (K < 0 || K > g->n) return fail(IM_EINVAL, "K=%d outside [0, n=%d]", K, g->n);
+  if (K > 0 && (!out_seeds || !out_sigma_R)) return fail(IM_EINVAL, "null output");
+  QueryParams q;
+  int rc = make_params(g, R, p, rng_seed, &q);
+  if (rc != IM_OK) return rc;
+  if (K == 0) return IM_OK;
+  std::lock_guard<std::mutex> lock(g->mu);
+  DeviceGuard dg(g->device);
+  im_workspace *ws = nullptr;
+  rc = internal_ws(g, R, &ws);
+  if (rc != IM_OK) return rc;
+  cudaStream_t s = t_stream;
+  rc = enqueue_select(g, ws, K, q, nullptr, ws->d_seeds_out, ws->d_sigma_out, s, false);
+  if (rc != IM_OK) return rc;
+  API_CUDA(cudaMemcpyAsync(out_seeds, ws->d_seeds_out, sizeof(int32_t) * K,
+                           cudaMemcpyDeviceToHost, s), "copy seeds");
+  API_CUDA(cudaMemcpyAsync(out_sigma_R, ws->d_sigma_out, sizeof(uint64_t) * K,
+                           cudaMemcpyDeviceToHost, s), "copy sigma");
+  return take_status(ws, s);
+}
+
+int im_estimate_spread(const im_graph *g_, const int32_t *seeds, int32_t num_seeds, int32_t R,
+                       double p, uint32_t rng_seed, uint64_t *out_sigma_R) {
+  if (!g_) return fail(IM_EINVAL, "null graph");
+  im_graph *g = const_cast<im_graph *>(g_);
+  if (num_seeds < 0) return fail(IM_EINVAL, "num_seeds < 0");
+  if (!out_sigma_R || (num_seeds > 0 && !seeds)) return fail(IM_EINVAL, "null argument");
+  for (int32_t i = 0; i < num_seeds; ++i)
+    if (seeds[i] < 0 || seeds[i] >= g->n) return fail(IM_EINVAL, "seed id %d out of range", seeds[i]);
+  QueryParams q;
+  int rc = make_params(g, R, p, rng_seed, &q);
+  if (rc != IM_OK) return rc;
+  std::lock_guard<std::mutex> lock(g->mu);
+  DeviceGuard dg(g->device);
+  im_workspace *ws = nullptr;
+  rc = internal_ws(g, R, &ws);
+  if (rc != IM_OK) return rc;
+  rc = ensure_seed_in(ws, num_seeds);
+  if (rc != IM_OK) return rc;
+  cudaStream_t s = t_stream;
+  if (num_seeds > 0)
+    API_CUDA(cudaMemcpyAsync(ws->d_seeds_in, seeds, sizeof(int32_t) * num_seeds,
+                             cudaMemcpyHostToDevice, s), "copy seeds");
+  rc = enqueue_spread(g, ws, ws->d_seeds_in, num_seeds, q, nullptr, ws->d_sigma_out, s);
+  if (rc != IM_OK) return rc;
+  API_CUDA(cudaMemcpyAsync(out_sigma_R, ws->d_sigma_out, sizeof(uint64_t),
+                           cudaMemcpyDeviceToHost, s), "copy sigma");
+  return take_status(ws, s);
+}
+
+// ------------------------------------------------------------------ test hooks
+
+static int debug_tables(const im_graph *g_, int32_t R, double p, uint32_t rng_seed,
+                        const uint8_t *h_mask, int32_t *out_labels, uint32_t *out_sizes) {
+  if (!g_) return fail(IM_EINVAL, "null graph");
+  im_graph *g = const_cast<im_graph *>(g_);
+  QueryParams q;
+  int rc = make_params(g, R, p, rng_seed, &q);
+  if (rc != IM_OK) return rc;
+  std::lock_guard<std::mutex> lock(g->mu);
+  DeviceGuard dg(g->device);
+  im_workspace *ws = nullptr;
+  rc = internal_ws(g, R, &ws);
+  if (rc != IM_OK) return rc;
+  cudaStream_t s = t_stream;
+  const uint8_t *d_mask = nullptr;
+  if (h_mask) {
+    const size_t bytes = (size_t)2 * g->m * R;
+    rc = ensure_mask(ws, bytes);
+    if (rc != IM_OK) return rc;
+    API_CUDA(cudaMemcpyAsync(ws->d_mask, h_mask, bytes, cudaMemcpyHostToDevice, s), "copy mask");
+    d_mask = ws->d_mask;
+  }
+  rc = enqueue_select(g, ws, 0, q, d_mask, nullptr, nullptr, s, true);
+  if (rc != IM_OK) return rc;
+  const size_t nR = (size_t)g->n * R;
+  int32_t *d_lab = nullptr;
+  uint32_t *d_siz = nullptr;
+  if (out_labels) API_CUDA(dalloc(&d_lab, nR), "cudaMalloc labels");
+  if (out_sizes) {
+    cudaError_t e = dalloc(&d_siz, nR);
+    if (e != cudaSuccess) {
+      if (d_lab) cudaFree(d_lab);
+      return cuda_fail(e, "cudaMalloc sizes");
+    }
+  }
+  cudaError_t e = launch_expand(g, ws, q, d_lab, d_siz, s);
+  if (e == cudaSuccess && d_lab)
+    e = cudaMemcpyAsync(out_labels, d_lab, sizeof(int32_t) * nR, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && d_siz)
+    e = cudaMemcpyAsync(out_sizes, d_siz, sizeof(uint32_t) * nR, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (d_lab) cudaFree(d_lab);
+  if (d_siz) cudaFree(d_siz);
+  if (e != cudaSuccess) return cuda_fail(e, "debug tables");
+  return take_status(ws, s);
+}
+
+int im_debug_labels(const im_graph *g, int32_t R, double p, uint32_t rng_seed,
+                    int32_t *out_labels) {
+  if (!out_labels) return fail(IM_EINVAL, "null output");
+  return debug_tables(g, R, p, rng_seed, nullptr, out_labels, nullptr);
+}
+
+int im_debug_sizes(const im_graph *g, int32_t R, double p, uint32_t rng_seed,
+                   uint32_t *out_sizes) {
+  if (!out_sizes) return fail(IM_EINVAL, "null output");
+  return debug_tables(g, R, p, rng_seed, nullptr, nullptr, out_sizes);
+}
+
+int im_debug_lane_randoms(int32_t R, uint32_t rng_seed, uint32_t *out_X) {
+  if (!out_X) return fail(IM_EINVAL, "null output");
+  QueryParams q;
+  int rc = make_params(nullptr, R, 0.5, rng_seed, &q);
+  if (rc != IM_OK) return rc;
+  im_graph g;
+  g.n = 1;
+  API_CUDA(cudaGetDevice(&g.device), "device");
+  API_CUDA(cudaDeviceGetAttribute(&g.num_sms, cudaDevAttrMultiProcessorCount, g.device), "attr");
+  im_workspace *ws = nullptr;
+  rc = ws_create(&g, R, &ws);
+  if (rc != IM_OK) return rc;
+  cudaStream_t s = t_stream;
+  cudaError_t e = launch_prep(ws, q, false, false, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(out_X, ws->d_X, sizeof(uint32_t) * R, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  ws_free(ws);
+  delete ws;
+  if (e != cudaSuccess) return cuda_fail(e, "lane randoms");
+  return IM_OK;
+}
+
+int im_debug_edge_hash(const int32_t *u, const int32_t *v, int64_t count, uint32_t *out_h) {
+  if (count < 0 || (count > 0 && (!u || !v || !out_h))) return fail(IM_EINVAL, "bad arguments");
+  if (count == 0) return IM_OK;
+  int32_t *du = nullptr, *dv = nullptr;
+  uint32_t *dh = nullptr;
+  cudaStream_t s = t_stream;
+  cudaError_t e = dalloc(&du, count);
+  if (e == cudaSuccess) e = dalloc(&dv, count);
+  if (e == cudaSuccess) e = dalloc(&dh, count);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(du, u, sizeof(int32_t) * count, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dv, v, sizeof(int32_t) * count, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = launch_edge_hash(du, dv, count, dh, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out_h, dh, sizeof(uint32_t) * count, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (du) cudaFree(du);
+  if (dv) cudaFree(dv);
+  if (dh) cudaFree(dh);
+  if (e != cudaSuccess) return cuda_fail(e, "edge hash");
+  return IM_OK;
+}
+
+int im_debug_select_seeds_masked(const im_graph *g_, int32_t K, int32_t R, const uint8_t *mask,
+                                 int32_t *out_seeds, uint64_t *out_sigma_R,
+                                 int32_t *out_labels, uint32_t *out_sizes) {
+  if (!g_ || !mask) return fail(IM_EINVAL, "null argument");
+  im_graph *g = const_cast<im_graph *>(g_);
+  if (K < 0 || K > g->n) return fail(IM_EINVAL, "K outside [0, n]");
+  if (K > 0 && (!out_seeds || !out_sigma_R)) return fail(IM_EINVAL, "null output");
+  if (out_labels || out_sizes) {
+    int rc = debug_tables(g, R, 0.5, 0, mask, out_labels, out_sizes);
+    if (rc != IM_OK) return rc;
+  }
+  if (K == 0) return IM_OK;
+  QueryParams q;
+  int rc = make_params(g, R, 0.5, 0, &q);
+  if (rc != IM_OK) return rc;
+  std::lock_guard<std::mutex> lock(g->mu);
+  DeviceGuard dg(g->device);
+  im_workspace *ws = nullptr;
+  rc = internal_ws(g, R, &ws);
+  if (rc != IM_OK) return rc;
+  cudaStream_t s = t_stream;
+  const size_t bytes = (size_t)2 * g->m * R;
+  rc = ensure_mask(ws, bytes);
+  if (rc != IM_OK) return rc;
+  API_CUDA(cudaMemcpyAsync(ws->d_mask, mask, bytes, cudaMemcpyHostToDevice, s), "copy mask");
+  rc = enqueue_select(g, ws, K, q, ws->d_mask, ws->d_seeds_out, ws->d_sigma_out, s, false);
+  if (rc != IM_OK) return rc;
+  API_CUDA(cudaMemcpyAsync(out_seeds, ws->d_seeds_out, sizeof(int32_t) * K,
+                           cudaMemcpyDeviceToHost, s), "copy seeds");
+  API_CUDA(cudaMemcpyAsync(out_sigma_R, ws->d_sigma_out, sizeof(uint64_t) * K,
+                           cudaMemcpyDeviceToHost, s), "copy sigma");
+  return take_status(ws, s);
+}
+
+int im_debug_estimate_spread_masked(const im_graph *g_, const int32_t *seeds, int32_t num_seeds,
+                                    int32_t R, const uint8_t *mask, uint64_t *out_sigma_R) {
+  if (!g_ || !mask || !out_sigma_R || num_seeds < 0 || (num_seeds > 0 && !seeds))
+    return fail(IM_EINVAL, "bad arguments");
+  im_graph *g = const_cast<im_graph *>(g_);
+  for (int32_t i = 0; i < num_seeds; ++i)
+    if (seeds[i] < 0 || seeds[i] >= g->n) return fail(IM_EINVAL, "seed id out of range");
+  QueryParams q;
+  int rc = make_params(g, R, 0.5, 0, &q);
+  if (rc != IM_OK) return rc;
+  std::lock_guard<std::mutex> lock(g->mu);
+  DeviceGuard dg(g->device);
+  im_workspace *ws = nullptr;
+  rc = internal_ws(g, R, &ws);
+  if (rc != IM_OK) return rc;
+  rc = ensure_seed_in(ws, num_seeds);
+  if (rc != IM_OK) return rc;
+  cudaStream_t s = t_stream;
+  const size_t bytes = (size_t)2 * g->m * R;
+  rc = ensure_mask(ws, bytes);
+  if (rc != IM_OK) return rc;
+  API_CUDA(cudaMemcpyAsync(ws->d_mask, mask, bytes, cudaMemcpyHostToDevice, s), "copy mask");
+  if (num_seeds > 0)
+    API_CUDA(cudaMemcpyAsync(ws->d_seeds_in, seeds, sizeof(int32_t) * num_seeds,
+                             cudaMemcpyHostToDevice, s), "copy seeds");
+  rc = enqueue_spread(g, ws, ws->d_seeds_in, num_seeds, q, ws->d_mask, ws->d_sigma_out, s);
+  if (rc != IM_OK) return rc;
+  API_CUDA(cudaMemcpyAsync(out_sigma_R, ws->d_sigma_out, sizeof(uint64_t),
+                           cudaMemcpyDeviceToHost, s), "copy sigma");
+  return take_status(ws, s);
+}
+
+}  // extern "C"
