@@ -262,10 +262,24 @@ def run_ours(args, xadj, adj, w):
     spread_h = d_spread.cpu().numpy().astype(np.uint64)
     consistent = bool(all(int(spread_h[i]) == int(sigma_h[i, -1]) for i in range(len(ps))))
 
-    # Per-kernel times: the same steps again with events around every launch.
+    # Per-kernel times: the same steps again with events around every launch,
+    # then each p on its own (kernel times and device work counters per query).
+    im.im_workspace_stats(ws)
     im.im_profile_enable(True)
     timed_steps(args.steps)
     prof = im.im_profile_read()
+    by_p = {}
+    for i, p in enumerate(ps):
+        im.im_profile_read()
+        im.im_workspace_stats(ws)
+        for _ in range(args.steps):
+            flush.zero_()
+            im.im_select_seeds_async(g, ws, K, R, p, seed, d_seeds[i], d_sigma[i])
+            im.im_estimate_spread_async(g, ws, d_seeds[i], K, R, p, seed, d_spread[i:i + 1])
+        pp = im.im_profile_read()
+        st = im.im_workspace_stats(ws)
+        by_p[str(p)] = {"avg_us": {k: round(v[0] / v[1] * 1e3, 2) for k, v in pp.items() if v[1]},
+                        "per_query": {k: v / args.steps for k, v in st.items()}}
     im.im_profile_enable(False)
 
     units_per_step = len(ps) * 2 * m * R
@@ -308,7 +322,7 @@ def run_ours(args, xadj, adj, w):
         "config": workload_config(args.workload, xadj, adj, w),
         "select_plus_spread_ms_per_query": total_ms / args.steps / len(ps),
         "gpu_launches": int(launches), "roofline": roof, "hbm_kernels": hbm,
-        "per_kernel": per_kernel, "clocks": clock_info, "consistent_spread": consistent,
+        "per_kernel": per_kernel, "per_p": by_p, "clocks": clock_info, "consistent_spread": consistent,
         "paper_context": "NetHEP (15,235 v / 58,892 e), K=50, p=0.01: 0.08 s on 2x Xeon "
                          "E5-2620v4, 16 threads (Table 4); R not stated",
     }

@@ -120,6 +120,30 @@ int im_estimate_spread_async(const im_graph *g, im_workspace *ws, const int32_t 
  * IM_EINTERNAL. */
 int im_workspace_status(im_workspace *ws);
 
+/* Work counters accumulated by the device since the last call (synchronizes
+ * the thread's stream, then clears them): */
+enum {
+  IM_STAT_CELF_ROUNDS = 0,       /* pool evaluation rounds of the lazy greedy */
+  IM_STAT_CELF_EVALUATIONS = 1,  /* exact marginal-gain evaluations */
+  IM_STAT_CELF_EXTRACTIONS = 2,  /* candidate prefixes extracted from the bounds */
+  IM_STAT_SPREAD_LEVELS = 3,     /* BFS levels of the spread estimates */
+  IM_STAT_CELF_CYC_EXTRACT = 4,  /* SM clock cycles of the CELF block in prefix extraction */
+  IM_STAT_CELF_CYC_EVAL = 5,     /* ... in exact gain evaluation */
+  IM_STAT_CELF_CYC_COMMIT = 6,   /* ... in commits and pool updates */
+  IM_STAT_CELF_CYC_MERGE = 7,    /* ... in merging survivors back */
+  IM_STAT_CELF_REFRESHES = 8,    /* grid-wide recomputations of all exact gains */
+  IM_STAT_CELF_CYC_PICK = 9,     /* commit loop: choosing the best pool member */
+  IM_STAT_CELF_CYC_BOOK = 10,    /* commit loop: recording the seed */
+  IM_STAT_CELF_CYC_UPDATE = 11,  /* commit loop: updating the other pool gains */
+  IM_STAT_CELF_CYC_COVER = 12,   /* marking the round's components covered */
+  IM_STAT_CHECK_CODE = 13,       /* first failed internal invariant check (0 = none) */
+  IM_STAT_CHECK_V0 = 14,         /* ... and two values describing it */
+  IM_STAT_CHECK_V1 = 15,
+  IM_NUM_STATS = 16
+};
+/* out: host array of IM_NUM_STATS int64 values. */
+int im_workspace_stats(im_workspace *ws, int64_t *out);
+
 /* ---------------------------------------------------------------- misc */
 
 /* Thread-local description of the last failure of this thread (valid until

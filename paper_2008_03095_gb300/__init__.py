@@ -13,4 +13,4 @@ from ._binding import (IM_EBUSY, IM_ECUDA, IM_EINTERNAL, IM_EINVAL, IM_ENOMEM, I
                        im_last_error, im_profile_enable, im_profile_read, PHASES,
                        im_sampling_threshold, im_select_seeds, im_select_seeds_async,
                        im_set_stream, im_workspace_create, im_workspace_destroy,
-                       im_workspace_status, lib, library_path)
+                       im_workspace_stats, im_workspace_status, lib, library_path, STATS)

@@ -62,6 +62,7 @@ def lib():
         "im_select_seeds_async": [P, P, i32, i32, f64, u32, P, P],
         "im_estimate_spread_async": [P, P, P, i32, i32, f64, u32, P],
         "im_workspace_status": [P],
+        "im_workspace_stats": [P, P],
         "im_set_stream": [P],
         "im_sampling_threshold": [f64, P],
         "im_debug_labels": [P, i32, f64, u32, P],
@@ -187,8 +188,8 @@ def im_graph_info(g):
 
 
 def im_select_seeds(g, K, R, p, rng_seed, out_seeds=None, out_sigma=None):
-    seeds = np.empty(K, dtype=np.int32) if out_seeds is None else out_seeds
-    sigma = np.empty(K, dtype=np.uint64) if out_sigma is None else out_sigma
+    seeds = np.empty(max(K, 0), dtype=np.int32) if out_seeds is None else out_seeds
+    sigma = np.empty(max(K, 0), dtype=np.uint64) if out_sigma is None else out_sigma
     _check(lib().im_select_seeds(_gh(g), K, R, p, rng_seed & 0xFFFFFFFF, _ptr(seeds), _ptr(sigma)))
     return seeds, sigma
 
@@ -223,6 +224,19 @@ def im_estimate_spread_async(g, ws, d_seeds, num_seeds, R, p, rng_seed, d_sigma)
 
 def im_workspace_status(ws):
     _check(lib().im_workspace_status(ws.handle))
+
+
+STATS = ("celf_rounds", "celf_evaluations", "celf_extractions", "spread_levels",
+         "celf_cycles_extract", "celf_cycles_eval", "celf_cycles_commit", "celf_cycles_merge",
+         "celf_refreshes", "celf_cycles_pick", "celf_cycles_book", "celf_cycles_update",
+         "celf_cycles_cover", "check_code", "check_v0", "check_v1")
+
+
+def im_workspace_stats(ws):
+    """{counter: value} accumulated on the device since the last call."""
+    out = np.zeros(len(STATS), dtype=np.int64)
+    _check(lib().im_workspace_stats(ws.handle, _ptr(out)))
+    return {name: int(out[i]) for i, name in enumerate(STATS)}
 
 
 def im_set_stream(stream):
@@ -289,8 +303,8 @@ def im_debug_edge_hash(u, v):
 def im_debug_select_seeds_masked(g, K, mask, tables=False):
     mask = np.ascontiguousarray(mask, dtype=np.uint8)
     R = mask.shape[1]
-    seeds = np.empty(K, dtype=np.int32)
-    sigma = np.empty(K, dtype=np.uint64)
+    seeds = np.empty(max(K, 0), dtype=np.int32)
+    sigma = np.empty(max(K, 0), dtype=np.uint64)
     lab = np.empty((g.n, R), dtype=np.int32) if tables else None
     siz = np.empty((g.n, R), dtype=np.uint32) if tables else None
     _check(lib().im_debug_select_seeds_masked(_gh(g), K, R, _ptr(mask), _ptr(seeds), _ptr(sigma),

@@ -127,11 +127,13 @@ cudaError_t dalloc(T **p, size_t count) {
 }
 
 void ws_free(im_workspace *ws) {
-  void *ptrs[] = {ws->d_P,    ws->d_cov,  ws->d_keys, ws->d_keyrange, ws->d_pool,
-                  ws->d_X,    ws->d_Xs,   ws->d_perm, ws->d_boff,     ws->d_sortbuf,
-                  ws->d_V,    ws->d_F0,   ws->d_F1,   ws->d_L0,       ws->d_L1,
-                  ws->d_inlist, ws->d_cnt, ws->d_acc, ws->d_status,   ws->d_seeds_out,
-                  ws->d_sigma_out, ws->d_seeds_in, ws->d_mask};
+  void *ptrs[] = {ws->d_P,      ws->d_cov,     ws->d_keys,      ws->d_keyrange, ws->d_pool,
+                  ws->d_X,      ws->d_Xs,      ws->d_perm,      ws->d_boff,     ws->d_sortbuf,
+                  ws->d_V,      ws->d_F0,      ws->d_F1,        ws->d_F2,       ws->d_L0,
+                  ws->d_L1,     ws->d_L2,      ws->d_Q0,        ws->d_Q1,       ws->d_Q2,
+                  ws->d_inlist, ws->d_cnt,     ws->d_acc,
+                  ws->d_stats,  ws->d_status,  ws->d_seeds_out, ws->d_sigma_out,
+                  ws->d_seeds_in, ws->d_mask,  ws->d_chosen,    ws->d_celf_ctl};
   for (void *p : ptrs)
     if (p) cudaFree(p);
 }
@@ -154,6 +156,8 @@ int ws_create(const im_graph *g, int32_t R_max, im_workspace **out) {
   WS_ALLOC(d_cov, (nR + 31) / 32);
   WS_ALLOC(d_keys, n);
   WS_ALLOC(d_keyrange, 2);
+  WS_ALLOC(d_chosen, n);
+  if (e == cudaSuccess) e = cudaMalloc(&ws->d_celf_ctl, celf_ctl_bytes());
   WS_ALLOC(d_pool, (size_t)R_max * 8 > (size_t)160 * 1024 ? (size_t)2 * 8 * R_max : 1);
   WS_ALLOC(d_X, R_max);
   WS_ALLOC(d_Xs, R_max);
@@ -163,16 +167,23 @@ int ws_create(const im_graph *g, int32_t R_max, im_workspace **out) {
   WS_ALLOC(d_V, n * W);
   WS_ALLOC(d_F0, n * W);
   WS_ALLOC(d_F1, n * W);
+  WS_ALLOC(d_F2, n * W);
   WS_ALLOC(d_L0, n);
   WS_ALLOC(d_L1, n);
+  WS_ALLOC(d_L2, n);
+  WS_ALLOC(d_Q0, n + (size_t)g->m / 16 + 1);
+  WS_ALLOC(d_Q1, n + (size_t)g->m / 16 + 1);
+  WS_ALLOC(d_Q2, n + (size_t)g->m / 16 + 1);
   WS_ALLOC(d_inlist, n);
-  WS_ALLOC(d_cnt, 4);
+  WS_ALLOC(d_cnt, 2 * (n + 4));
   WS_ALLOC(d_acc, 1);
+  WS_ALLOC(d_stats, IM_NUM_STATS);
   WS_ALLOC(d_status, 1);
   WS_ALLOC(d_seeds_out, n);
   WS_ALLOC(d_sigma_out, n);
 #undef WS_ALLOC
   if (e == cudaSuccess) e = cudaMemset(ws->d_status, 0, sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMemset(ws->d_stats, 0, sizeof(unsigned long long) * IM_NUM_STATS);
   if (e != cudaSuccess) {
     ws_free(ws);
     delete ws;
@@ -413,6 +424,18 @@ int im_workspace_status(im_workspace *ws) {
   if (!ws) return fail(IM_EINVAL, "null workspace");
   DeviceGuard dg(ws->device);
   return take_status(ws, t_stream);
+}
+
+int im_workspace_stats(im_workspace *ws, int64_t *out) {
+  if (!ws || !out) return fail(IM_EINVAL, "null argument");
+  DeviceGuard dg(ws->device);
+  unsigned long long h[IM_NUM_STATS];
+  cudaStream_t s = t_stream;
+  API_CUDA(cudaMemcpyAsync(h, ws->d_stats, sizeof(h), cudaMemcpyDeviceToHost, s), "stats copy");
+  API_CUDA(cudaMemsetAsync(ws->d_stats, 0, sizeof(h), s), "stats clear");
+  API_CUDA(cudaStreamSynchronize(s), "stream synchronize");
+  for (int i = 0; i < IM_NUM_STATS; ++i) out[i] = (int64_t)h[i];
+  return IM_OK;
 }
 
 int im_select_seeds_async(const im_graph *g, im_workspace *ws, int32_t K, int32_t R, double p,

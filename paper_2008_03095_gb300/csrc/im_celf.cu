@@ -1,6 +1,7 @@
 // On-device lazy greedy (CELF) seed selection over the memoized samples
-// (Algorithm 7 lines 3-18; CELF of Section 2.2), one persistent 1024-thread
-// block per query.
+// (Algorithm 7 lines 3-18; CELF of Section 2.2): one cooperative launch with
+// one 1024-thread block per SM. Block 0 drives the lazy greedy; all blocks
+// join for the grid-wide steps (prefix extraction and bulk gain refresh).
 //
 // Keys pack (gain << 32) | (0xffffffff - v): a larger key means a larger gain
 // and, on equal gains, a smaller vertex id, so the key order is exactly the
@@ -8,25 +9,37 @@
 // exact and unique.
 //
 // State:
-//   keys[n]    initial upper bounds (the NewGreedy-step gains mg_v) in global
-//              memory; C, a prefix of at most kCap candidates extracted from it
-//              in key order, lives in shared memory with its current bounds.
+//   keys[n]    upper bounds of every vertex (initially the NewGreedy-step
+//              gains mg_v) in global memory; C, a prefix of at most kCap
+//              candidates extracted from it in key order, lives in the
+//              driver's shared memory, sorted descending, with current bounds.
 //   sig_out    the largest key of any vertex outside C (0 if none).
-//   pool       up to B candidates evaluated exactly against the current seed
-//              set: per lane, the component root and the (not yet covered)
+//   pool       the first B entries of C, evaluated exactly against the current
+//              seed set: per lane, the component root and the not yet covered
 //              component size, kept in shared memory.
-// Round: take the top-B keys of C into the pool and evaluate them (the
-// segmented reduce of Algorithm 7 lines 14-16). While the best pool gain beats
-// every other bound (C's largest and sig_out), commit it (lines 11-12): mark
-// its components covered in the per-sample bitmap and subtract, from every
-// other pool member, the lanes it shares a component with -- so pool gains stay
-// exact and several seeds can be committed per round. Remaining pool members
-// return to C with their exact gains as new bounds (submodularity keeps them
-// valid). If everything in C falls below sig_out, C is written back and the
-// next prefix is extracted. The committed sequence equals naive greedy with
-// lowest-id tie-break: a committed key is exact and exceeds every bound, and
-// bounds dominate true gains.
+// Round (driver): evaluate the pool (the segmented reduce of Algorithm 7 lines
+// 14-16). While the best pool gain beats every other bound (the head of the
+// rest of C and sig_out), commit it (lines 11-12) and subtract, from every
+// other pool member, the lanes it shares a component with -- pool gains stay
+// exact, so several seeds can be committed per round. The round's seeds mark
+// their components covered in the per-sample bitmap; surviving pool members
+// are merged back into C with their exact gains as new bounds (submodularity
+// keeps them valid). The committed sequence equals naive greedy with lowest-id
+// tie-break: a committed key is exact and exceeds every bound.
+// Grid steps:
+//   extraction  when the head of C falls below sig_out, C is written back and
+//               all blocks find the next prefix (histogram threshold search
+//               over the bounds, then compaction).
+//   refresh     when many candidates were evaluated without a commit (a large
+//               component just got covered, so many bounds are loose), all
+//               blocks recompute every exact gain against the current seed set
+//               (a full NewGreedy step on the memoized samples) and the prefix
+//               is extracted again from these exact keys.
+#include <cooperative_groups.h>
+
 #include "im_common.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace imgb {
 
@@ -34,9 +47,22 @@ constexpr int kCelfThreads = 1024;
 constexpr int kCelfWarps = kCelfThreads / 32;
 constexpr int kCap = 4096;     // candidate prefix capacity
 constexpr int kTarget = 2048;  // prefix size aimed for per extraction
+constexpr int kBins = 2048;    // histogram bins of the threshold search
 constexpr int kPoolMax = 32;
 constexpr size_t kPoolSmemBudget = 160 * 1024;
-constexpr uint32_t kRoundCap = 1u << 22;
+
+enum : int { kCmdExtract = 1, kCmdRefresh = 2, kCmdDone = 3, kCmdFail = 4 };
+
+// Grid-shared control block (global memory).
+struct CelfCtl {
+  unsigned long long kmin, kmax, sig_out;
+  unsigned int kcount, nC;
+  int cmd, pad;
+  unsigned int hist[3][kBins];
+  unsigned long long C[kCap];
+};
+
+size_t celf_ctl_bytes() { return sizeof(CelfCtl); }
 
 int celf_pool_size(uint32_t R) {
   const size_t per = (size_t)R * 8;
@@ -53,29 +79,31 @@ struct CelfArgs {
   uint32_t *cov;
   uint64_t *keys;
   const uint64_t *keyrange;
+  uint8_t *chosen;
+  CelfCtl *ctl;
   uint32_t n, R;
   int K;
   int B;
   int pool_smem;
+  uint32_t refresh_after;  // evaluations without a commit that trigger a refresh
+  uint32_t round_cap;      // budget of driver rounds (see launch_celf)
   uint32_t *g_pool;
   int32_t *out_seeds;
   uint64_t *out_sigma;
   int32_t *status;
+  unsigned long long *stats;
 };
 
 struct CelfSmem {
   uint64_t C[kCap];
-  uint64_t bmin[256];
-  uint64_t bmax[256];
-  uint32_t hist[256];
+  uint32_t hist[kBins];
   uint64_t red[kCelfWarps];
-  uint32_t redc[kCelfWarps];
   int32_t pid[kPoolMax];
-  int32_t pslot[kPoolMax];
   uint32_t pgain[kPoolMax];
   int32_t pactive[kPoolMax];
-  uint32_t nC;
-  uint32_t npool;
+  int32_t committed[kPoolMax];
+  uint64_t Y[kPoolMax];
+  uint32_t ny, ncommit;
   uint64_t sel_t, sel_A, sel_B;
   uint32_t sel_above;
   int sel_done;
@@ -89,143 +117,123 @@ __device__ __forceinline__ uint64_t make_key(uint32_t gain, int32_t v) {
 __device__ __forceinline__ int32_t key_vertex(uint64_t k) {
   return (int32_t)(0xffffffffu - (uint32_t)k);
 }
+__device__ __forceinline__ uint64_t umax64(uint64_t a, uint64_t b) { return a > b ? a : b; }
+__device__ __forceinline__ uint64_t umin64(uint64_t a, uint64_t b) { return a < b ? a : b; }
 
-__device__ uint64_t block_max_u64(uint64_t v, CelfSmem &s) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+__device__ __forceinline__ uint64_t warp_max_u64(uint64_t v) {
 #pragma unroll
-  for (int d = 16; d > 0; d >>= 1) {
-    uint64_t o = __shfl_xor_sync(kFull, v, d);
-    v = o > v ? o : v;
-  }
-  if (lane == 0) s.red[warp] = v;
-  __syncthreads();
-  if (warp == 0) {
-    v = s.red[lane];
+  for (int d = 16; d > 0; d >>= 1) v = umax64(v, __shfl_xor_sync(kFull, v, d));
+  return v;
+}
+__device__ __forceinline__ uint64_t warp_min_u64(uint64_t v) {
 #pragma unroll
-    for (int d = 16; d > 0; d >>= 1) {
-      uint64_t o = __shfl_xor_sync(kFull, v, d);
-      v = o > v ? o : v;
-    }
-    if (lane == 0) s.red[0] = v;
-  }
-  __syncthreads();
-  v = s.red[0];
-  __syncthreads();
+  for (int d = 16; d > 0; d >>= 1) v = umin64(v, __shfl_xor_sync(kFull, v, d));
   return v;
 }
 
-__device__ uint64_t block_min_u64(uint64_t v, CelfSmem &s) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int d = 16; d > 0; d >>= 1) {
-    uint64_t o = __shfl_xor_sync(kFull, v, d);
-    v = o < v ? o : v;
+// ------------------------------------------------------------------ grid steps
+
+// Grid-wide min / max / count of the valid keys (nonzero, < hi) into ctl.
+__device__ void grid_key_stats(const CelfArgs &a, uint64_t hi) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t gtid = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t gthreads = gridDim.x * blockDim.x;
+  uint64_t mn = ~0ull, mx = 0ull;
+  uint32_t c = 0;
+  for (uint32_t i = gtid; i < a.n; i += gthreads) {
+    const uint64_t k = __ldcg(a.keys + i);
+    if (k == 0 || k >= hi) continue;
+    mn = umin64(mn, k);
+    mx = umax64(mx, k);
+    ++c;
   }
-  if (lane == 0) s.red[warp] = v;
-  __syncthreads();
-  if (warp == 0) {
-    v = s.red[lane];
+  mn = warp_min_u64(mn);
+  mx = warp_max_u64(mx);
 #pragma unroll
-    for (int d = 16; d > 0; d >>= 1) {
-      uint64_t o = __shfl_xor_sync(kFull, v, d);
-      v = o < v ? o : v;
-    }
-    if (lane == 0) s.red[0] = v;
+  for (int d = 16; d > 0; d >>= 1) c += __shfl_xor_sync(kFull, c, d);
+  if (lane == 0 && c) {
+    atomicMin(&a.ctl->kmin, (unsigned long long)mn);
+    atomicMax(&a.ctl->kmax, (unsigned long long)mx);
+    atomicAdd(&a.ctl->kcount, c);
   }
-  __syncthreads();
-  v = s.red[0];
-  __syncthreads();
-  return v;
 }
 
-__device__ uint32_t block_sum_u32(uint32_t v, CelfSmem &s) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(kFull, v, d);
-  if (lane == 0) s.redc[warp] = v;
-  __syncthreads();
-  if (warp == 0) {
-    v = s.redc[lane];
-#pragma unroll
-    for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(kFull, v, d);
-    if (lane == 0) s.redc[0] = v;
-  }
-  __syncthreads();
-  v = s.redc[0];
-  __syncthreads();
-  return v;
-}
-
-// Radix-style threshold search. Valid keys: nonzero and (if bounded) < hi.
-// A, B, nvalid: minimum, maximum and count of the valid keys. Returns t such
-// that the valid keys >= t number between min(target, nvalid) and cap. Each
-// pass histograms the 8 bits below the highest bit in which the current range
-// [A, B] differs, then either stops at the bucket where the count crosses the
-// target or narrows the range to that bucket.
-__device__ uint64_t select_threshold(const uint64_t *keys, uint32_t cnt, bool bounded,
-                                     uint64_t hi, uint64_t A, uint64_t B, uint32_t nvalid,
-                                     uint32_t target, uint32_t cap, CelfSmem &s,
-                                     int32_t *status) {
-  if (nvalid <= cap) return A;
+// Threshold search over the valid keys (nonzero and, if bounded, < hi) of
+// keys[0..n): every block returns the same t such that the number of valid
+// keys >= t lies in [min(target, count), cap]. Each pass histograms the
+// current range [A, B] into kBins equal bins (shared-memory counts per block,
+// summed into a global histogram), finds the bin where the running count from
+// the top reaches the target, and stops there if everything down to that bin
+// fits in cap, else narrows to that bin. Global histograms rotate over three
+// buffers so that one grid barrier per pass suffices.
+__device__ __noinline__ uint64_t grid_select(const CelfArgs &a, cg::grid_group &grid, bool bounded,
+                                uint64_t hi, uint64_t A, uint64_t B, uint32_t target,
+                                uint32_t cap, CelfSmem &s, uint32_t &pass_id) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint32_t gthreads = gridDim.x * blockDim.x;
   uint32_t above = 0;
-  for (int pass = 0; pass < 66; ++pass) {
-    if (A == B) return A;
-    const int hb = 63 - __clzll((long long)(A ^ B));
-    const int shift = hb >= 7 ? hb - 7 : 0;
-    const uint64_t base = A >> shift;
-    for (int i = tid; i < 256; i += blockDim.x) {
-      s.hist[i] = 0;
-      s.bmin[i] = ~0ull;
-      s.bmax[i] = 0ull;
-    }
+  for (int pass = 0; pass < 8; ++pass) {
+    const uint32_t buf = pass_id % 3, zbuf = (pass_id + 1) % 3;
+    ++pass_id;
+    const uint64_t span = B - A;
+    const int bl = span ? 64 - __clzll((long long)span) : 0;
+    const int shift = bl > 11 ? bl - 11 : 0;
+    if (blockIdx.x == gridDim.x - 1)
+      for (int i = tid; i < kBins; i += blockDim.x) a.ctl->hist[zbuf][i] = 0u;
+    for (int i = tid; i < kBins; i += blockDim.x) s.hist[i] = 0u;
     __syncthreads();
-    for (uint32_t i = tid; i < cnt; i += blockDim.x) {
-      const uint64_t k = keys[i];
-      if (k == 0 || (bounded && k >= hi) || k < A || k > B) continue;
-      const uint32_t d = (uint32_t)((k >> shift) - base);
-      atomicAdd(&s.hist[d], 1u);
-      atomicMin((unsigned long long *)&s.bmin[d], (unsigned long long)k);
-      atomicMax((unsigned long long *)&s.bmax[d], (unsigned long long)k);
-    }
-    __syncthreads();
-    if (warp == 0) {
-      uint32_t c8[8];
-      uint32_t lsum = 0;
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        c8[i] = s.hist[255 - 8 * lane - i];
-        lsum += c8[i];
+    for (uint32_t base = blockIdx.x * blockDim.x + (uint32_t)warp * 32; base < a.n;
+         base += gthreads) {
+      const uint32_t i = base + lane;
+      const uint64_t k = i < a.n ? __ldcg(a.keys + i) : 0ull;
+      const bool in = k != 0 && (!bounded || k < hi) && k >= A && k <= B;
+      const unsigned act = __ballot_sync(kFull, in);
+      if (in) {
+        const uint32_t d = (uint32_t)((k - A) >> shift);
+        const unsigned peers = __match_any_sync(act, d);
+        if (lane == __ffs(peers) - 1) atomicAdd(&s.hist[d], (uint32_t)__popc(peers));
       }
+    }
+    __syncthreads();
+    for (int i = tid; i < kBins; i += blockDim.x)
+      if (s.hist[i]) atomicAdd(&a.ctl->hist[buf][i], s.hist[i]);
+    grid.sync();
+    if (warp == 0) {
+      // lane l covers bins 2047-64l down to 1984-64l
+      uint32_t lsum = 0;
+      for (int i = 0; i < 64; ++i) lsum += __ldcg(&a.ctl->hist[buf][kBins - 1 - 64 * lane - i]);
       uint32_t incl = lsum;
 #pragma unroll
       for (int d = 1; d < 32; d <<= 1) {
-        uint32_t t = __shfl_up_sync(kFull, incl, d);
+        const uint32_t t = __shfl_up_sync(kFull, incl, d);
         if (lane >= d) incl += t;
       }
       const uint32_t excl = incl - lsum;
       const unsigned ball = __ballot_sync(kFull, above + incl >= target);
-      const int L = ball ? __ffs(ball) - 1 : -1;
-      if (L < 0 && lane == 0) {  // cannot happen: the range holds >= target keys
-        s.sel_done = 1;
-        s.sel_t = A;
-        set_status(status, IM_EINTERNAL);
-      }
-      if (lane == L) {
-        uint32_t cum = above + excl;
-        int d = 255 - 8 * lane;
-        for (int i = 0; i < 8; ++i) {
-          d = 255 - 8 * lane - i;
-          if (cum + c8[i] >= target) break;
-          cum += c8[i];
-        }
-        if (cum + s.hist[d] <= cap) {
+      if (!ball) {  // fewer valid keys than the target: take the whole range
+        if (lane == 0) {
           s.sel_done = 1;
-          s.sel_t = s.bmin[d];
+          s.sel_t = A;
+        }
+      } else if (lane == __ffs(ball) - 1) {
+        uint32_t cum = above + excl;
+        int d = kBins - 1 - 64 * lane;
+        uint32_t hd = 0;
+        for (int i = 0; i < 64; ++i) {
+          d = kBins - 1 - 64 * lane - i;
+          hd = __ldcg(&a.ctl->hist[buf][d]);
+          if (cum + hd >= target) break;
+          cum += hd;
+        }
+        const uint64_t lo = A + ((uint64_t)d << shift);
+        if (cum + hd <= cap || shift == 0) {
+          s.sel_done = 1;
+          s.sel_t = lo;
         } else {
           s.sel_done = 0;
-          s.sel_A = s.bmin[d];
-          s.sel_B = s.bmax[d];
+          s.sel_A = lo;
+          const uint64_t top = lo + (((uint64_t)1 << shift) - 1);
+          s.sel_B = top < B ? top : B;
           s.sel_above = cum;
         }
       }
@@ -241,180 +249,319 @@ __device__ uint64_t select_threshold(const uint64_t *keys, uint32_t cnt, bool bo
     above = s.sel_above;
     __syncthreads();
   }
-  set_status(status, IM_EINTERNAL);
+  if (tid == 0) set_status(a.status, IM_EINTERNAL);
   return A;
 }
 
-__global__ void __launch_bounds__(kCelfThreads, 1) k_celf(CelfArgs a) {
-  __shared__ CelfSmem s;
-  extern __shared__ uint32_t dyn[];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+// Grid-wide compaction of the valid keys >= t into ctl->C, and the largest
+// valid key below t into ctl->sig_out.
+__device__ void grid_compact(const CelfArgs &a, bool bounded, uint64_t hi, uint64_t t) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t gthreads = gridDim.x * blockDim.x;
+  uint64_t below = 0;
+  for (uint32_t base = blockIdx.x * blockDim.x + (uint32_t)warp * 32; base < a.n;
+       base += gthreads) {
+    const uint32_t i = base + lane;
+    const uint64_t k = i < a.n ? __ldcg(a.keys + i) : 0ull;
+    const bool valid = k != 0 && (!bounded || k < hi);
+    const bool take = valid && k >= t;
+    if (valid && !take) below = umax64(below, k);
+    const unsigned ball = __ballot_sync(kFull, take);
+    if (ball) {
+      uint32_t base_pos = 0;
+      if (lane == __ffs(ball) - 1) base_pos = atomicAdd(&a.ctl->nC, (uint32_t)__popc(ball));
+      base_pos = __shfl_sync(kFull, base_pos, __ffs(ball) - 1);
+      const uint32_t pos = base_pos + __popc(ball & ((1u << lane) - 1u));
+      if (take && pos < (uint32_t)kCap) a.ctl->C[pos] = k;
+    }
+  }
+  below = warp_max_u64(below);
+  if (lane == 0 && below) atomicMax(&a.ctl->sig_out, (unsigned long long)below);
+}
+
+// Exact gain of every vertex against the current seed set (covered bitmap),
+// chosen vertices excluded; keys rewritten, key statistics into ctl.
+__device__ __noinline__ void grid_refresh(const CelfArgs &a) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
   const uint32_t R = a.R;
-  const int B = a.B;
-  uint32_t *proot = a.pool_smem ? dyn : a.g_pool;
-  uint32_t *pcont = proot + (size_t)B * R;
-
-  int nsel = 0;
-  uint64_t sigma = 0;  // meaningful in thread 0
-  bool bounded = false;
-  uint64_t hi = 0;
-  uint64_t sig_out = 0;
-  bool need_extract = true;
-  if (tid == 0) s.nC = 0;
-  __syncthreads();
-
-  for (uint32_t round = 0; nsel < a.K; ++round) {
-    if (round >= kRoundCap) {
-      if (tid == 0) set_status(a.status, IM_ETIMEOUT);
-      break;
-    }
-    // ---------------------------------------------------------- extraction
-    if (need_extract) {
-      const uint32_t nC = s.nC;
-      for (uint32_t i = tid; i < nC; i += blockDim.x) {
-        const uint64_t k = s.C[i];
-        if (k) a.keys[key_vertex(k)] = k;
-      }
-      __syncthreads();
-      uint64_t A, Bk;
-      uint32_t nvalid;
-      if (!bounded) {
-        A = a.keyrange[0];
-        Bk = a.keyrange[1];
-        nvalid = a.n;
-      } else {
-        uint64_t mn = ~0ull, mx = 0ull;
-        uint32_t c = 0;
-        for (uint32_t i = tid; i < a.n; i += blockDim.x) {
-          const uint64_t k = a.keys[i];
-          if (k == 0 || k >= hi) continue;
-          mn = k < mn ? k : mn;
-          mx = k > mx ? k : mx;
-          ++c;
-        }
-        A = block_min_u64(mn, s);
-        Bk = block_max_u64(mx, s);
-        nvalid = block_sum_u32(c, s);
-      }
-      if (nvalid == 0) {  // no vertex left anywhere: cannot happen with K <= n
-        if (tid == 0) set_status(a.status, IM_EINTERNAL);
-        break;
-      }
-      const uint64_t t = select_threshold(a.keys, a.n, bounded, hi, A, Bk, nvalid, kTarget,
-                                          kCap, s, a.status);
-      if (tid == 0) s.nC = 0;
-      __syncthreads();
-      uint64_t below = 0;
-      for (uint32_t i = tid; i < a.n; i += blockDim.x) {
-        const uint64_t k = a.keys[i];
-        if (k == 0 || (bounded && k >= hi)) continue;
-        if (k >= t) {
-          const uint32_t pos = atomicAdd(&s.nC, 1u);
-          if (pos < (uint32_t)kCap) s.C[pos] = k;
-        } else if (k > below) {
-          below = k;
-        }
-      }
-      sig_out = block_max_u64(below, s);  // includes a barrier
-      if (s.nC > (uint32_t)kCap) {
-        if (tid == 0) set_status(a.status, IM_EINTERNAL);
-        break;
-      }
-      bounded = true;
-      hi = t;
-      need_extract = false;
-    }
-
-    // ---------------------------------------------------------- pool = top-B of C
-    const uint32_t nC = s.nC;
-    uint64_t mn = ~0ull, mx = 0ull;
-    uint32_t c = 0;
-    for (uint32_t i = tid; i < nC; i += blockDim.x) {
-      const uint64_t k = s.C[i];
-      if (!k) continue;
-      mn = k < mn ? k : mn;
-      mx = k > mx ? k : mx;
-      ++c;
-    }
-    const uint64_t cA = block_min_u64(mn, s);
-    const uint64_t cB = block_max_u64(mx, s);
-    const uint32_t cvalid = block_sum_u32(c, s);
-    uint64_t kc = 0;
-    if (tid == 0) s.npool = 0;
-    __syncthreads();
-    if (cvalid > 0) {
-      const uint64_t tB =
-          select_threshold(s.C, nC, false, 0, cA, cB, cvalid, (uint32_t)B, (uint32_t)B, s, a.status);
-      uint64_t below = 0;
-      for (uint32_t i = tid; i < nC; i += blockDim.x) {
-        const uint64_t k = s.C[i];
-        if (!k) continue;
-        if (k >= tB) {
-          const uint32_t p = atomicAdd(&s.npool, 1u);
-          if (p < (uint32_t)B) {
-            s.pid[p] = key_vertex(k);
-            s.pslot[p] = (int32_t)i;
-            s.pactive[p] = 1;
-            s.C[i] = 0;
-          }
-        } else if (k > below) {
-          below = k;
-        }
-      }
-      kc = block_max_u64(below, s);
-    }
-    const uint32_t npool = s.npool < (uint32_t)B ? s.npool : (uint32_t)B;
-    const uint64_t top_out = kc > sig_out ? kc : sig_out;
-
-    // ---------------------------------------------------------- exact gains
-    // g(u | S) = sum_r [component of u in r not covered] * |C_r(u)|
-    if ((uint32_t)warp < npool) {
-      const int32_t u = s.pid[warp];
-      uint32_t *rr = proot + (size_t)warp * R;
-      uint32_t *cc = pcont + (size_t)warp * R;
-      const int32_t *row = a.P + (size_t)u * R;
-      for (uint32_t j = lane; j < R; j += 32) rr[j] = (uint32_t)__ldg(row + j);
+  uint64_t mn = ~0ull, mx = 0ull;
+  uint32_t c = 0;
+  for (uint32_t v = gwarp; v < a.n; v += nwarps) {
+    uint64_t key = 0;
+    if (!__ldcg(a.chosen + v)) {
+      const int32_t *row = a.P + (size_t)v * R;
       uint32_t g = 0;
+#pragma unroll 4
       for (uint32_t j = lane; j < R; j += 32) {
-        const int32_t x = (int32_t)rr[j];
-        uint32_t root, sz;
-        bool maybe_cov;
-        if (x < 0) {
-          root = (uint32_t)u;
-          sz = (uint32_t)(-x);
-          maybe_cov = x != -1;  // a singleton {u} is covered only if u is a seed
-        } else {
-          root = (uint32_t)x;
-          sz = (uint32_t)(-__ldg(a.P + (size_t)x * R + j));
-          maybe_cov = true;
-        }
-        uint32_t cv = sz;
-        if (maybe_cov) {
-          const uint32_t bit = root * R + j;
-          if ((__ldcg(a.cov + (bit >> 5)) >> (bit & 31)) & 1u) cv = 0;
-        }
-        rr[j] = root;
-        cc[j] = cv;
-        g += cv;
+        const int32_t x = __ldg(row + j);
+        const uint32_t root = x < 0 ? v : (uint32_t)x;
+        const uint32_t sz = x < 0 ? (uint32_t)(-x) : (uint32_t)(-__ldg(a.P + (size_t)x * R + j));
+        const uint32_t bit = root * R + j;
+        const uint32_t cw = (x != -1) ? __ldcg(a.cov + (bit >> 5)) : 0u;
+        g += ((cw >> (bit & 31)) & 1u) ? 0u : sz;
       }
 #pragma unroll
       for (int d = 16; d > 0; d >>= 1) g += __shfl_xor_sync(kFull, g, d);
+      key = make_key(g, (int32_t)v);
+      mn = umin64(mn, key);
+      mx = umax64(mx, key);
+      ++c;
+    }
+    if (lane == 0) a.keys[v] = key;
+  }
+  if (lane == 0 && c) {
+    atomicMin(&a.ctl->kmin, (unsigned long long)mn);
+    atomicMax(&a.ctl->kmax, (unsigned long long)mx);
+    atomicAdd(&a.ctl->kcount, c);
+  }
+}
+
+// Single-block versions of the extraction steps, used by the driver alone when
+// n is small enough that grid barriers would cost more than the work.
+constexpr uint32_t kLocalN = 65536;
+
+__device__ uint64_t block_reduce_u64(uint64_t v, bool is_max, CelfSmem &s) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  v = is_max ? warp_max_u64(v) : warp_min_u64(v);
+  if (lane == 0) s.red[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    v = s.red[lane];
+    v = is_max ? warp_max_u64(v) : warp_min_u64(v);
+    if (lane == 0) s.red[0] = v;
+  }
+  __syncthreads();
+  v = s.red[0];
+  __syncthreads();
+  return v;
+}
+
+__device__ __noinline__ uint64_t block_select(const CelfArgs &a, bool bounded, uint64_t hi, uint64_t A,
+                                 uint64_t B, uint32_t target, uint32_t cap, CelfSmem &s) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  uint32_t above = 0;
+  for (int pass = 0; pass < 8; ++pass) {
+    const uint64_t span = B - A;
+    const int bl = span ? 64 - __clzll((long long)span) : 0;
+    const int shift = bl > 11 ? bl - 11 : 0;
+    for (int i = tid; i < kBins; i += blockDim.x) s.hist[i] = 0u;
+    __syncthreads();
+    for (uint32_t base = (uint32_t)warp * 32; base < a.n; base += blockDim.x) {
+      const uint32_t i = base + lane;
+      const uint64_t k = i < a.n ? __ldcg(a.keys + i) : 0ull;
+      const bool in = k != 0 && (!bounded || k < hi) && k >= A && k <= B;
+      const unsigned act = __ballot_sync(kFull, in);
+      if (in) {
+        const uint32_t d = (uint32_t)((k - A) >> shift);
+        const unsigned peers = __match_any_sync(act, d);
+        if (lane == __ffs(peers) - 1) atomicAdd(&s.hist[d], (uint32_t)__popc(peers));
+      }
+    }
+    __syncthreads();
+    if (warp == 0) {
+      uint32_t lsum = 0;
+      for (int i = 0; i < 64; ++i) lsum += s.hist[kBins - 1 - 64 * lane - i];
+      uint32_t incl = lsum;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t t = __shfl_up_sync(kFull, incl, d);
+        if (lane >= d) incl += t;
+      }
+      const uint32_t excl = incl - lsum;
+      const unsigned ball = __ballot_sync(kFull, above + incl >= target);
+      if (!ball) {
+        if (lane == 0) {
+          s.sel_done = 1;
+          s.sel_t = A;
+        }
+      } else if (lane == __ffs(ball) - 1) {
+        uint32_t cum = above + excl;
+        int d = kBins - 1 - 64 * lane;
+        uint32_t hd = 0;
+        for (int i = 0; i < 64; ++i) {
+          d = kBins - 1 - 64 * lane - i;
+          hd = s.hist[d];
+          if (cum + hd >= target) break;
+          cum += hd;
+        }
+        const uint64_t lo = A + ((uint64_t)d << shift);
+        if (cum + hd <= cap || shift == 0) {
+          s.sel_done = 1;
+          s.sel_t = lo;
+        } else {
+          s.sel_done = 0;
+          s.sel_A = lo;
+          const uint64_t top = lo + (((uint64_t)1 << shift) - 1);
+          s.sel_B = top < B ? top : B;
+          s.sel_above = cum;
+        }
+      }
+    }
+    __syncthreads();
+    if (s.sel_done) {
+      const uint64_t t = s.sel_t;
+      __syncthreads();
+      return t;
+    }
+    A = s.sel_A;
+    B = s.sel_B;
+    above = s.sel_above;
+    __syncthreads();
+  }
+  if (tid == 0) set_status(a.status, IM_EINTERNAL);
+  return A;
+}
+
+// Valid keys >= t into s.C (returns the count) and the largest key below t.
+__device__ __noinline__ uint32_t block_compact(const CelfArgs &a, bool bounded, uint64_t hi, uint64_t t,
+                                  CelfSmem &s, uint64_t &sig_out) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) s.ny = 0;  // reused as the fill counter
+  __syncthreads();
+  uint64_t below = 0;
+  for (uint32_t base = (uint32_t)warp * 32; base < a.n; base += blockDim.x) {
+    const uint32_t i = base + lane;
+    const uint64_t k = i < a.n ? __ldcg(a.keys + i) : 0ull;
+    const bool valid = k != 0 && (!bounded || k < hi);
+    const bool take = valid && k >= t;
+    if (valid && !take) below = umax64(below, k);
+    const unsigned ball = __ballot_sync(kFull, take);
+    if (ball) {
+      uint32_t base_pos = 0;
+      if (lane == __ffs(ball) - 1) base_pos = atomicAdd(&s.ny, (uint32_t)__popc(ball));
+      base_pos = __shfl_sync(kFull, base_pos, __ffs(ball) - 1);
+      const uint32_t pos = base_pos + __popc(ball & ((1u << lane) - 1u));
+      if (take && pos < (uint32_t)kCap) s.C[pos] = k;
+    }
+  }
+  sig_out = block_reduce_u64(below, true, s);  // barriers
+  return s.ny;
+}
+
+// Descending bitonic sort of s.C[0..npow2) (entries past nC padded with 0).
+__device__ __noinline__ void sort_desc(CelfSmem &s, uint32_t nC) {
+  uint32_t npow2 = 1;
+  while (npow2 < nC) npow2 <<= 1;
+  for (uint32_t i = nC + threadIdx.x; i < npow2; i += blockDim.x) s.C[i] = 0ull;
+  __syncthreads();
+  for (uint32_t k = 2; k <= npow2; k <<= 1) {
+    for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+      for (uint32_t i = threadIdx.x; i < npow2; i += blockDim.x) {
+        const uint32_t ixj = i ^ j;
+        if (ixj > i) {
+          const uint64_t x = s.C[i], y = s.C[ixj];
+          const bool desc = (i & k) == 0;
+          if ((x < y) == desc) {
+            s.C[i] = y;
+            s.C[ixj] = x;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// ------------------------------------------------------------------ driver state
+struct Driver {
+  int nsel = 0;
+  uint64_t sigma = 0;  // thread 0
+  uint32_t head = 0, nC = 0;
+  uint64_t sig_out = 0;
+  uint32_t rounds = 0, evals = 0, evals_since_commit = 0;
+  unsigned long long cyc[4] = {0, 0, 0, 0};
+};
+
+// Block 0: lazy-greedy rounds over the prefix in shared memory until the
+// query is done or a grid step is needed. Returns the next command. POOL_SMEM:
+// the per-lane pool arrays live in shared memory (else in global memory).
+template <bool POOL_SMEM>
+__device__ __noinline__ int drive_rounds(const CelfArgs &a, CelfSmem &s, uint32_t *proot, uint32_t *pcont,
+                            Driver &d) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint32_t R = a.R;
+  const uint32_t B = (uint32_t)a.B;
+  long long t_mark = clock64();
+  for (;;) {
+    if (d.nsel >= a.K) return kCmdDone;
+    if (d.rounds >= a.round_cap) {
+      if (tid == 0) set_status(a.status, IM_ETIMEOUT);
+      return kCmdFail;
+    }
+    if (d.head >= d.nC || s.C[d.head] < d.sig_out) return kCmdExtract;
+    if (d.evals_since_commit >= a.refresh_after) {
+      d.evals_since_commit = 0;  // the refresh makes every key exact
+      return kCmdRefresh;
+    }
+    ++d.rounds;
+    const uint32_t np = (d.nC - d.head) < B ? (d.nC - d.head) : B;
+    if (tid < (int)np) {
+      s.pid[tid] = key_vertex(s.C[d.head + tid]);
+      s.pactive[tid] = 1;
+    }
+    if (tid == 0) s.ncommit = 0;
+    const uint64_t kc = d.head + np < d.nC ? s.C[d.head + np] : 0ull;
+    const uint64_t top_out = umax64(kc, d.sig_out);
+    d.evals += np;
+    d.evals_since_commit += np;
+    __syncthreads();
+
+    // ---------------------------------------------------------- exact gains
+    // g(u | S) = sum_r [component of u in r not covered] * |C_r(u)|. All
+    // (candidate, lane) items are spread over the block; the loads of an item
+    // depend only on its label-table slot, so they overlap across items.
+    const uint32_t items = np * R;
+    for (uint32_t i = tid; i < items; i += blockDim.x) {
+      const uint32_t c = i / R, j = i - c * R;
+      proot[i] = (uint32_t)__ldg(a.P + (size_t)s.pid[c] * R + j);
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (uint32_t i = tid; i < items; i += blockDim.x) {
+      const uint32_t c = i / R, j = i - c * R;
+      const uint32_t u = (uint32_t)s.pid[c];
+      const int32_t x = (int32_t)proot[i];
+      const uint32_t root = x < 0 ? u : (uint32_t)x;
+      const uint32_t bit = root * R + j;
+      // a singleton {u} (x == -1) is covered only if u is a seed
+      const uint32_t sz = x < 0 ? (uint32_t)(-x) : (uint32_t)(-__ldg(a.P + (size_t)x * R + j));
+      const uint32_t cw = (x != -1) ? __ldcg(a.cov + (bit >> 5)) : 0u;
+      proot[i] = root;
+      pcont[i] = ((cw >> (bit & 31)) & 1u) ? 0u : sz;
+    }
+    __syncthreads();
+    if ((uint32_t)warp < np) {
+      const uint32_t *cc = pcont + (size_t)warp * R;
+      uint32_t g = 0;
+      if ((R & 3u) == 0) {
+        const uint4 *c4 = reinterpret_cast<const uint4 *>(cc);
+        for (uint32_t q = lane; q < (R >> 2); q += 32) {
+          const uint4 v = c4[q];
+          g += v.x + v.y + v.z + v.w;
+        }
+      } else {
+        for (uint32_t j = lane; j < R; j += 32) g += cc[j];
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(kFull, g, o);
       if (lane == 0) s.pgain[warp] = g;
     }
     __syncthreads();
+    {
+      const long long t_now = clock64();
+      d.cyc[1] += (unsigned long long)(t_now - t_mark);
+      t_mark = t_now;
+    }
 
     // ---------------------------------------------------------- commits
     uint64_t bk = 0;
     for (;;) {
       if (warp == 0) {
         uint64_t k = 0;
-        if ((uint32_t)lane < npool && s.pactive[lane]) k = make_key(s.pgain[lane], s.pid[lane]);
-        uint64_t best = k;
-#pragma unroll
-        for (int d = 16; d > 0; d >>= 1) {
-          uint64_t o = __shfl_xor_sync(kFull, best, d);
-          best = o > best ? o : best;
-        }
+        if ((uint32_t)lane < np && s.pactive[lane]) k = make_key(s.pgain[lane], s.pid[lane]);
+        const uint64_t best = warp_max_u64(k);
         const unsigned b = __ballot_sync(kFull, k != 0 && k == best);
         if (lane == 0) {
           s.best_key = best;
@@ -426,50 +573,284 @@ __global__ void __launch_bounds__(kCelfThreads, 1) k_celf(CelfArgs a) {
       const int bw = s.best_w;
       if (bk == 0 || bk < top_out) break;
       if (tid == 0) {
-        sigma += s.pgain[bw];
-        a.out_seeds[nsel] = s.pid[bw];
-        a.out_sigma[nsel] = sigma;
+        d.sigma += s.pgain[bw];
+        a.out_seeds[d.nsel] = s.pid[bw];
+        a.out_sigma[d.nsel] = d.sigma;
+        a.chosen[s.pid[bw]] = 1;
         s.pactive[bw] = 0;
+        s.committed[s.ncommit++] = bw;
       }
-      ++nsel;
-      const uint32_t *rb = proot + (size_t)bw * R;
-      const uint32_t *cb = pcont + (size_t)bw * R;
-      for (uint32_t j = tid; j < R; j += blockDim.x) {
-        if (cb[j]) {
-          const uint32_t bit = rb[j] * R + j;
-          atomicOr(a.cov + (bit >> 5), 1u << (bit & 31));
-        }
-      }
+      ++d.nsel;
+      d.evals_since_commit = 0;
       __syncthreads();
-      if (nsel >= a.K) break;
-      if ((uint32_t)warp < npool && s.pactive[warp]) {
+      if (d.nsel >= a.K) break;
+      if ((uint32_t)warp < np && s.pactive[warp]) {
+        const uint32_t *rb = proot + (size_t)bw * R;
         const uint32_t *rr = proot + (size_t)warp * R;
         uint32_t *cc = pcont + (size_t)warp * R;
-        uint32_t d = 0;
-        for (uint32_t j = lane; j < R; j += 32) {
-          const uint32_t cv = cc[j];
-          if (cv && rr[j] == rb[j]) {
-            d += cv;
-            cc[j] = 0;
+        uint32_t dsum = 0;
+        if ((R & 3u) == 0) {
+          const uint4 *rb4 = reinterpret_cast<const uint4 *>(rb);
+          const uint4 *rr4 = reinterpret_cast<const uint4 *>(rr);
+          uint4 *cc4 = reinterpret_cast<uint4 *>(cc);
+          for (uint32_t q = lane; q < (R >> 2); q += 32) {
+            uint4 cv = cc4[q];
+            if (!(cv.x | cv.y | cv.z | cv.w)) continue;
+            const uint4 r = rr4[q], b = rb4[q];
+            bool dirty = false;
+            if (cv.x && r.x == b.x) { dsum += cv.x; cv.x = 0; dirty = true; }
+            if (cv.y && r.y == b.y) { dsum += cv.y; cv.y = 0; dirty = true; }
+            if (cv.z && r.z == b.z) { dsum += cv.z; cv.z = 0; dirty = true; }
+            if (cv.w && r.w == b.w) { dsum += cv.w; cv.w = 0; dirty = true; }
+            if (dirty) cc4[q] = cv;
+          }
+        } else {
+          for (uint32_t j = lane; j < R; j += 32) {
+            const uint32_t cv = cc[j];
+            if (cv && rr[j] == rb[j]) {
+              dsum += cv;
+              cc[j] = 0;
+            }
           }
         }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(kFull, d, o);
-        if (lane == 0) s.pgain[warp] -= d;
+        for (int o = 16; o > 0; o >>= 1) dsum += __shfl_xor_sync(kFull, dsum, o);
+        if (lane == 0) s.pgain[warp] -= dsum;
       }
       __syncthreads();
     }
-    if (nsel >= a.K) break;
-    // ---------------------------------------------------------- back to C
-    if (warp == 0 && (uint32_t)lane < npool && s.pactive[lane])
-      s.C[s.pslot[lane]] = make_key(s.pgain[lane], s.pid[lane]);
-    __threadfence();
-    __syncthreads();
-    if (bk == 0 && kc == 0 && sig_out == 0) {
-      if (tid == 0) set_status(a.status, IM_EINTERNAL);
-      break;
+    // The round's seeds cover their components: the lanes whose contribution
+    // is still > 0 are exactly those no earlier seed had covered.
+    {
+      const uint32_t ncm = s.ncommit;
+      for (uint32_t i = tid; i < ncm * R; i += blockDim.x) {
+        const uint32_t c = (uint32_t)s.committed[i / R], j = i % R;
+        if (pcont[(size_t)c * R + j]) {
+          const uint32_t bit = proot[(size_t)c * R + j] * R + j;
+          atomicOr(a.cov + (bit >> 5), 1u << (bit & 31));
+        }
+      }
     }
-    need_extract = sig_out > kc;
+    {
+      const long long t_now = clock64();
+      d.cyc[2] += (unsigned long long)(t_now - t_mark);
+      t_mark = t_now;
+    }
+    if (d.nsel >= a.K) {
+      __syncthreads();
+      return kCmdDone;
+    }
+
+    // ---------------------------------------------------------- merge survivors back
+    if (warp == 0) {
+      const bool alive = (uint32_t)lane < np && s.pactive[lane];
+      uint64_t y = alive ? make_key(s.pgain[lane], s.pid[lane]) : 0ull;
+#pragma unroll
+      for (int k = 2; k <= 32; k <<= 1) {  // bitonic sort across the warp, descending
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+          const uint64_t o = __shfl_xor_sync(kFull, y, j);
+          const bool lower = (lane & j) == 0;
+          const bool desc = (lane & k) == 0;
+          y = (lower == desc) ? umax64(o, y) : umin64(o, y);
+        }
+      }
+      s.Y[lane] = y;
+      const unsigned ball = __ballot_sync(kFull, alive);
+      if (lane == 0) s.ny = __popc(ball);
+    }
+    __syncthreads();
+    {
+      const uint32_t ny = s.ny;
+      const uint32_t xs = d.head + np;  // rest of C: [xs, nC), sorted descending
+      const uint32_t L = d.nC - xs;
+      const uint32_t ob = xs - ny;      // merged output starts here
+      uint64_t vx[kCap / kCelfThreads];
+      uint32_t px[kCap / kCelfThreads];
+#pragma unroll
+      for (int q = 0; q < kCap / kCelfThreads; ++q) {
+        const uint32_t i = (uint32_t)tid + (uint32_t)q * kCelfThreads;
+        vx[q] = 0;
+        px[q] = 0;
+        if (i < L) {
+          const uint64_t x = s.C[xs + i];
+          uint32_t lo = 0, h2 = ny;  // number of Y greater than x
+          while (lo < h2) {
+            const uint32_t mid = (lo + h2) >> 1;
+            if (s.Y[mid] > x) lo = mid + 1; else h2 = mid;
+          }
+          vx[q] = x;
+          px[q] = ob + i + lo;
+        }
+      }
+      uint64_t vy = 0;
+      uint32_t py = 0;
+      if ((uint32_t)tid < ny) {
+        vy = s.Y[tid];
+        uint32_t lo = 0, h2 = L;  // number of X greater than y
+        while (lo < h2) {
+          const uint32_t mid = (lo + h2) >> 1;
+          if (s.C[xs + mid] > vy) lo = mid + 1; else h2 = mid;
+        }
+        py = ob + tid + lo;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int q = 0; q < kCap / kCelfThreads; ++q)
+        if ((uint32_t)tid + (uint32_t)q * kCelfThreads < L) s.C[px[q]] = vx[q];
+      if ((uint32_t)tid < ny) s.C[py] = vy;
+      d.head = ob;
+    }
+    __syncthreads();
+    {
+      const long long t_now = clock64();
+      d.cyc[3] += (unsigned long long)(t_now - t_mark);
+      t_mark = t_now;
+    }
+  }
+}
+
+template <bool POOL_SMEM>
+__global__ void __launch_bounds__(kCelfThreads, 1) k_celf(CelfArgs a) {
+  cg::grid_group grid = cg::this_grid();
+  __shared__ CelfSmem s;
+  extern __shared__ uint32_t dyn[];
+  const int tid = threadIdx.x;
+  const bool driver = blockIdx.x == 0;
+  const uint32_t gtid = blockIdx.x * blockDim.x + tid;
+  const uint32_t gthreads = gridDim.x * blockDim.x;
+  const uint32_t R = a.R;
+  uint32_t *proot = POOL_SMEM ? dyn : a.g_pool;
+  uint32_t *pcont = proot + (size_t)a.B * R;
+  CelfCtl *ctl = a.ctl;
+  const bool local_extract = a.n <= kLocalN;
+
+  for (uint32_t i = gtid; i < 3 * kBins; i += gthreads) (&ctl->hist[0][0])[i] = 0u;
+  for (uint32_t i = gtid; i < a.n; i += gthreads) a.chosen[i] = 0;
+  if (gtid == 0) {
+    ctl->kmin = ~0ull;
+    ctl->kmax = 0ull;
+    ctl->kcount = 0u;
+    ctl->nC = 0u;
+    ctl->sig_out = 0ull;
+    ctl->cmd = 0;
+  }
+  grid.sync();
+
+  Driver d;
+  bool bounded = false;
+  uint64_t hi = 0;
+  uint64_t A0 = a.keyrange[0], B0 = a.keyrange[1];
+  uint32_t pass_id = 0, extracts = 0, refreshes = 0;
+  int cmd = kCmdExtract;
+  uint32_t outer = 0;
+  for (; outer < a.round_cap; ++outer) {
+    const long long t0 = clock64();
+    if (cmd == kCmdRefresh) {
+      grid_refresh(a);
+      grid.sync();
+      A0 = __ldcg(&ctl->kmin);
+      B0 = __ldcg(&ctl->kmax);
+      bounded = false;
+      hi = 0;
+      ++refreshes;
+    }
+    // ---------------------------------------------------------- extraction
+    bool ok = true;
+    if (local_extract) {
+      if (driver) {
+        uint64_t A = A0, B = B0;
+        if (bounded) {
+          uint64_t mn = ~0ull, mx = 0ull;
+          for (uint32_t i = tid; i < a.n; i += blockDim.x) {
+            const uint64_t k = __ldcg(a.keys + i);
+            if (k == 0 || k >= hi) continue;
+            mn = umin64(mn, k);
+            mx = umax64(mx, k);
+          }
+          A = block_reduce_u64(mn, false, s);
+          B = block_reduce_u64(mx, true, s);
+        }
+        if (B == 0 || A > B) {  // no vertex left anywhere: cannot happen with K <= n
+          ok = false;
+        } else {
+          const uint64_t t = block_select(a, bounded, hi, A, B, kTarget, kCap, s);
+          uint64_t so = 0;
+          d.nC = block_compact(a, bounded, hi, t, s, so);
+          d.sig_out = so;
+          hi = t;
+        }
+        if (tid == 0) {  // accumulators of the next grid step
+          ctl->kmin = ~0ull;
+          ctl->kmax = 0ull;
+          ctl->kcount = 0u;
+        }
+      }
+    } else {
+      uint64_t A = A0, B = B0;
+      if (bounded) {
+        grid_key_stats(a, hi);
+        grid.sync();
+        A = __ldcg(&ctl->kmin);
+        B = __ldcg(&ctl->kmax);
+      }
+      if (B == 0 || A > B) {  // no vertex left anywhere: cannot happen with K <= n
+        if (gtid == 0) set_status(a.status, IM_EINTERNAL);
+        break;
+      }
+      const uint64_t t = grid_select(a, grid, bounded, hi, A, B, kTarget, kCap, s, pass_id);
+      grid_compact(a, bounded, hi, t);
+      grid.sync();
+      hi = t;
+      if (driver) {
+        const uint32_t nC = __ldcg(&ctl->nC);
+        d.nC = nC;
+        d.sig_out = __ldcg(&ctl->sig_out);
+        if (nC <= (uint32_t)kCap)
+          for (uint32_t i = tid; i < nC; i += blockDim.x) s.C[i] = __ldcg(&ctl->C[i]);
+        __syncthreads();
+        if (tid == 0) {  // accumulators for the next extraction
+          ctl->nC = 0u;
+          ctl->sig_out = 0ull;
+          ctl->kmin = ~0ull;
+          ctl->kmax = 0ull;
+          ctl->kcount = 0u;
+        }
+      }
+    }
+    bounded = true;
+    ++extracts;
+    // ---------------------------------------------------------- rounds (driver)
+    if (driver) {
+      if (!ok || d.nC > (uint32_t)kCap || d.nC == 0) {
+        if (tid == 0) set_status(a.status, IM_EINTERNAL);
+        cmd = kCmdFail;
+      } else {
+        d.head = 0;
+        sort_desc(s, d.nC);
+        d.cyc[0] += (unsigned long long)(clock64() - t0);
+        cmd = drive_rounds<POOL_SMEM>(a, s, proot, pcont, d);
+        if (cmd == kCmdExtract) {  // write the bounds of C back before the next search
+          for (uint32_t i = d.head + tid; i < d.nC; i += blockDim.x) {
+            const uint64_t k = s.C[i];
+            a.keys[key_vertex(k)] = k;
+          }
+        }
+      }
+      __syncthreads();
+      if (tid == 0) ctl->cmd = cmd;
+    }
+    grid.sync();
+    cmd = __ldcg(&ctl->cmd);
+    if (cmd == kCmdDone || cmd == kCmdFail) break;
+  }
+  if (outer >= a.round_cap && gtid == 0) set_status(a.status, IM_ETIMEOUT);
+  if (driver && tid == 0 && a.stats) {
+    atomicAdd(a.stats + 0, (unsigned long long)d.rounds);
+    atomicAdd(a.stats + 1, (unsigned long long)d.evals);
+    atomicAdd(a.stats + 2, (unsigned long long)extracts);
+    for (int i = 0; i < 4; ++i) atomicAdd(a.stats + 4 + i, d.cyc[i]);
+    atomicAdd(a.stats + 8, (unsigned long long)refreshes);
   }
 }
 
@@ -481,21 +862,41 @@ cudaError_t launch_celf(const im_graph *g, const im_workspace *ws, const QueryPa
   a.cov = ws->d_cov;
   a.keys = ws->d_keys;
   a.keyrange = ws->d_keyrange;
+  a.chosen = ws->d_chosen;
+  a.ctl = reinterpret_cast<CelfCtl *>(ws->d_celf_ctl);
   a.n = (uint32_t)g->n;
   a.R = q.R;
   a.K = K;
   a.B = celf_pool_size(q.R);
   a.pool_smem = celf_pool_in_smem(q.R) ? 1 : 0;
+  // A full refresh costs about n evaluations spread over the whole GPU; the
+  // driver block alone is ~100x slower per evaluation, so refresh once it has
+  // spent ~n/64 evaluations without committing.
+  uint32_t ra = (uint32_t)g->n / 64;
+  if (ra < (uint32_t)(4 * a.B)) ra = (uint32_t)(4 * a.B);
+  a.refresh_after = ra;
+  // Every round evaluates at least one candidate, fewer than refresh_after
+  // evaluations separate two commits or a commit and a refresh, and the
+  // round after a refresh commits (its keys are exact); every grid step is
+  // followed by at least one round.
+  a.round_cap = (uint32_t)(K + 2) * (ra + 8) + 1024;
   a.g_pool = ws->d_pool;
   a.out_seeds = d_seeds;
   a.out_sigma = d_sigma;
   a.status = ws->d_status;
+  a.stats = ws->d_stats;
   const size_t dyn = a.pool_smem ? (size_t)2 * a.B * q.R * sizeof(uint32_t) : 0;
-  cudaError_t e = cudaFuncSetAttribute(k_celf, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  const void *fn = a.pool_smem ? (const void *)k_celf<true> : (const void *)k_celf<false>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)kPoolSmemBudget);
   if (e != cudaSuccess) return e;
-  k_celf<<<1, kCelfThreads, dyn, s>>>(a);
-  return cudaGetLastError();
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kCelfThreads, dyn);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  dim3 grid(g->num_sms), block(kCelfThreads);
+  void *args[] = {&a};
+  return cudaLaunchCooperativeKernel(fn, grid, block, args, dyn, s);
 }
 
 }  // namespace imgb

@@ -155,6 +155,8 @@ struct im_workspace {
   uint64_t *d_keys = nullptr;   // n CELF keys (gain << 32 | ~id)
   uint64_t *d_keyrange = nullptr;  // [min, max] of the keys
   uint32_t *d_pool = nullptr;   // CELF pool spill: 2 * kPool * R_max words
+  uint8_t *d_chosen = nullptr;  // n flags: vertex already selected
+  void *d_celf_ctl = nullptr;   // grid-shared CELF control block
   // lanes
   uint32_t *d_X = nullptr;      // R_max raw X_r
   uint32_t *d_Xs = nullptr;     // R_max X in internal lane order
@@ -162,11 +164,14 @@ struct im_workspace {
   uint32_t *d_boff = nullptr;   // 2^kMaxBucketBits + 1 bucket offsets
   uint32_t *d_sortbuf = nullptr;  // lane sort scratch for large R
   // spread path
-  uint32_t *d_V = nullptr, *d_F0 = nullptr, *d_F1 = nullptr;  // n * W words each
-  int32_t *d_L0 = nullptr, *d_L1 = nullptr;                   // frontier lists (n)
-  uint32_t *d_inlist = nullptr;                                // n flags
-  uint32_t *d_cnt = nullptr;                                   // counters
+  uint32_t *d_V = nullptr;                                     // visited, n * W words
+  uint32_t *d_F0 = nullptr, *d_F1 = nullptr, *d_F2 = nullptr;  // frontiers, n * W words each
+  int32_t *d_L0 = nullptr, *d_L1 = nullptr, *d_L2 = nullptr;   // frontier lists (n)
+  uint64_t *d_Q0 = nullptr, *d_Q1 = nullptr, *d_Q2 = nullptr;  // chunk lists (n + 2m/32)
+  uint32_t *d_inlist = nullptr;                                // n level stamps
+  uint32_t *d_cnt = nullptr;                                   // 2(n + 4) per-level counts
   unsigned long long *d_acc = nullptr;                         // sigma accumulator
+  unsigned long long *d_stats = nullptr;                       // IM_NUM_STATS counters
   // status and blocking-call staging
   int32_t *d_status = nullptr;
   int32_t *d_seeds_out = nullptr;  // n
@@ -204,6 +209,7 @@ int graph_build_device(im_graph *g, const int32_t *h_xadj, const int32_t *h_adj,
 
 // shared-memory need of the CELF kernel for a given R (pool in smem or spilled)
 int celf_pool_size(uint32_t R);
+size_t celf_ctl_bytes();
 size_t lane_sort_smem(uint32_t R);
 
 }  // namespace imgb

@@ -94,9 +94,13 @@ struct PrepArgs {
 __device__ void prep_lanes(const PrepArgs &a, uint32_t *s_sort) {
   __shared__ uint32_t mt[624];
   const int t = threadIdx.x;
-  if (t == 0) {
-    mt[0] = a.seed;
-    for (int i = 1; i < 624; ++i) mt[i] = 1812433253u * (mt[i - 1] ^ (mt[i - 1] >> 30)) + (uint32_t)i;
+  if (t == 0) {  // the seeding recurrence is sequential; keep it in a register
+    uint32_t x = a.seed;
+    mt[0] = x;
+    for (int i = 1; i < 624; ++i) {
+      x = 1812433253u * (x ^ (x >> 30)) + (uint32_t)i;
+      mt[i] = x;
+    }
   }
   __syncthreads();
   for (uint32_t base = 0; base < a.R; base += 624) {

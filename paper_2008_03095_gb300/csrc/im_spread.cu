@@ -2,13 +2,19 @@
 // |union_{s in S} C_r(s)| (Algorithm 4 evaluated on the samples of Eq. 2).
 //
 // Bit-parallel multi-source BFS over all R samples at once: every vertex has an
-// R-bit visited mask V and a frontier mask F (bit j = internal lane j). One
-// level expands every frontier vertex u: for each neighbour v the edge hash
-// selects the lane bucket that can be live (the same bucket test as the
-// component kernel), the live bits of that bucket are built word by word, and
-// v gains F[u] & live & ~V[v] (atomicOr on V[v] decides who won each bit).
-// Newly set bits form v's next frontier mask and are counted into sigmaR.
-// Levels are separated by grid-wide barriers of one cooperative launch.
+// R-bit visited mask V and a frontier mask F (bit j = internal lane j). A level
+// is a list of work chunks (a frontier vertex u and 32 of its arcs), one warp
+// per chunk, so hubs spread over many warps. The warp holds u's frontier row
+// in registers; for each arc u->v the edge hash selects the lane bucket that
+// can be live (the same bucket test as the component kernel), and only the
+// lanes of that bucket that are in u's frontier are tested against Eq. 2. v
+// gains the live frontier lanes it has not seen (atomicOr on V[v] decides who
+// won each bit); newly set bits form v's next frontier mask and are counted
+// into sigmaR.
+// Three frontier buffers rotate so that one grid-wide barrier per level
+// suffices: level L reads F[L%3], writes F[(L+1)%3] and clears the rows of
+// the level L-1 frontier in F[(L+2)%3]. Per-level counters and level stamps
+// (instead of reset flags) build the frontier lists.
 #include <cooperative_groups.h>
 
 #include "im_common.cuh"
@@ -27,14 +33,43 @@ struct SpreadArgs {
   const uint8_t *mask;  // explicit-mask test mode: mask[arc * R + j]
   const int32_t *seeds;
   int num_seeds;
-  uint32_t *V, *F0, *F1;
-  int32_t *L0, *L1;
-  uint32_t *inlist;
-  uint32_t *cnt;  // [2] frontier sizes
+  uint32_t *V;
+  uint32_t *F[3];
+  int32_t *L[3];         // frontier vertices per level (for clearing F rows)
+  uint64_t *Q[3];        // frontier work chunks per level: (vertex << 32) | chunk
+  uint32_t *stamp;       // n: last list index (+1) a vertex was appended to
+  uint32_t *cntlev;      // n + 4: frontier vertices per level
+  uint32_t *chklev;      // n + 4: frontier chunks per level
   unsigned long long *acc;
   uint64_t *out;
   int32_t *status;
+  unsigned long long *stats;
 };
+
+template <class T>
+__device__ __forceinline__ T pick3(T a0, T a1, T a2, uint32_t i) {
+  return i == 0 ? a0 : (i == 1 ? a1 : a2);
+}
+
+__device__ __forceinline__ uint32_t lane_range_mask(uint32_t w, uint32_t j0, uint32_t j1) {
+  const uint32_t b0 = w << 5;
+  const uint32_t lo = j0 > b0 ? j0 - b0 : 0u;
+  const uint32_t hi = j1 < b0 + 32u ? j1 - b0 : 32u;
+  const uint32_t upper = hi >= 32u ? 0xffffffffu : ((1u << hi) - 1u);
+  return upper & ~((1u << lo) - 1u);
+}
+
+// Append v to frontier list `lev` with one work chunk per 32 arcs.
+__device__ __forceinline__ void push_frontier(const SpreadArgs &a, int32_t v, uint32_t lev,
+                                              int32_t *Ln, uint64_t *Qn) {
+  Ln[atomicAdd(a.cntlev + lev, 1u)] = v;
+  const uint32_t deg = (uint32_t)(a.xadj[v + 1] - a.xadj[v]);
+  const uint32_t nch = (deg + 31u) >> 5;
+  if (nch) {
+    const uint32_t at = atomicAdd(a.chklev + lev, nch);
+    for (uint32_t c = 0; c < nch; ++c) Qn[at + c] = ((uint64_t)(uint32_t)v << 32) | c;
+  }
+}
 
 __global__ void __launch_bounds__(512) k_spread(SpreadArgs a) {
   cg::grid_group grid = cg::this_grid();
@@ -47,110 +82,141 @@ __global__ void __launch_bounds__(512) k_spread(SpreadArgs a) {
 
   for (uint64_t i = tid; i < nW; i += nthr) {
     a.V[i] = 0u;
-    a.F0[i] = 0u;
-    a.F1[i] = 0u;
+    a.F[0][i] = 0u;
+    a.F[1][i] = 0u;
+    a.F[2][i] = 0u;
   }
-  for (uint64_t i = tid; i < a.n; i += nthr) a.inlist[i] = 0u;
-  if (tid < 2) a.cnt[tid] = 0u;
+  for (uint64_t i = tid; i < a.n; i += nthr) a.stamp[i] = 0u;
+  for (uint64_t i = tid; i < (uint64_t)a.n + 4; i += nthr) {
+    a.cntlev[i] = 0u;
+    a.chklev[i] = 0u;
+  }
   if (tid == 0) *a.acc = 0ull;
   grid.sync();
 
-  // sources: deduplicated seed set, all R lanes reached
+  // sources: deduplicated seed set (list 0, stamp 1), all R lanes reached
   for (uint64_t i = tid; i < (uint64_t)a.num_seeds; i += nthr) {
     const int32_t s = a.seeds[i];
     if (s < 0 || (uint32_t)s >= a.n) {
       set_status(a.status, IM_EINVAL);
       continue;
     }
-    if (atomicCAS(a.inlist + s, 0u, 1u) == 0u) a.L0[atomicAdd(a.cnt, 1u)] = s;
+    if (atomicMax(a.stamp + s, 1u) < 1u) push_frontier(a, s, 0, a.L[0], a.Q[0]);
   }
   grid.sync();
-  const uint32_t c0 = __ldcg(a.cnt);
+  const uint32_t c0 = __ldcg(a.cntlev);
   const uint32_t lastmask = (a.R & 31u) ? ((1u << (a.R & 31u)) - 1u) : 0xffffffffu;
   for (uint64_t i = tid; i < (uint64_t)c0 * W; i += nthr) {
     const uint32_t k = (uint32_t)(i / W), w = (uint32_t)(i % W);
     const uint32_t m = (w == W - 1) ? lastmask : 0xffffffffu;
-    const uint64_t o = (uint64_t)a.L0[k] * W + w;
+    const uint64_t o = (uint64_t)a.L[0][k] * W + w;
     a.V[o] = m;
-    a.F0[o] = m;
+    a.F[0][o] = m;
   }
-  for (uint64_t i = tid; i < c0; i += nthr) a.inlist[a.L0[i]] = 0u;
-  unsigned long long local = 0;
-  if (tid == 0) local = (unsigned long long)c0 * a.R;
+  unsigned long long local = (tid == 0) ? (unsigned long long)c0 * a.R : 0ull;
   grid.sync();
 
-  int32_t *Lc = a.L0, *Ln = a.L1;
-  uint32_t *Fc = a.F0, *Fn = a.F1;
-  int par = 0;
+  const bool row_in_regs = W <= 64;
   uint32_t level = 0;
-  for (; level <= a.n + 1; ++level) {
-    const uint32_t cc = __ldcg(a.cnt + par);
+  for (; level < a.n + 2; ++level) {
+    const uint32_t cc = __ldcg(a.cntlev + level);
     if (cc == 0) break;
-    for (uint64_t i = gwarp; i < cc; i += nwarps) {
-      const int32_t u = Lc[i];
-      const int32_t beg = a.xadj[u], end = a.xadj[u + 1];
+    const uint32_t nq = __ldcg(a.chklev + level);
+    const uint64_t *Qc = pick3(a.Q[0], a.Q[1], a.Q[2], level % 3);
+    int32_t *Ln = pick3(a.L[0], a.L[1], a.L[2], (level + 1) % 3);
+    uint64_t *Qn = pick3(a.Q[0], a.Q[1], a.Q[2], (level + 1) % 3);
+    const uint32_t *Fc = pick3(a.F[0], a.F[1], a.F[2], level % 3);
+    uint32_t *Fn = pick3(a.F[0], a.F[1], a.F[2], (level + 1) % 3);
+    const uint32_t next_stamp = level + 2;
+    // clear the frontier rows of level-1 (buffer (level+2)%3 is written next level)
+    if (level > 0) {
+      const uint32_t cp = __ldcg(a.cntlev + level - 1);
+      const int32_t *Lp = pick3(a.L[0], a.L[1], a.L[2], (level + 2) % 3);
+      uint32_t *Fp = pick3(a.F[0], a.F[1], a.F[2], (level + 2) % 3);
+      for (uint64_t i = tid; i < (uint64_t)cp * W; i += nthr)
+        Fp[(uint64_t)Lp[i / W] * W + (i % W)] = 0u;
+    }
+    // one warp per chunk of 32 arcs of a frontier vertex
+    for (uint64_t q = gwarp; q < nq; q += nwarps) {
+      const uint64_t qe = Qc[q];
+      const int32_t u = (int32_t)(qe >> 32);
+      const uint32_t ch = (uint32_t)qe;
       const uint32_t *fu = Fc + (uint64_t)u * W;
-      for (int32_t e = beg + lane; e < end; e += 32) {
-        const int32_t v = a.adj[e];
-        if (v == u) continue;
-        uint32_t j0, j1, h = 0;
-        if (a.mask) {
-          j0 = 0;
-          j1 = a.R;
-        } else {
-          h = edge_hash(u, v);
-          const uint32_t b = lane_bucket(h, a.nb);
-          j0 = __ldg(a.boff + b);
-          j1 = __ldg(a.boff + b + 1);
-        }
-        if (j0 >= j1) continue;
-        for (uint32_t w = j0 >> 5; w <= (j1 - 1) >> 5; ++w) {
-          const uint32_t f = __ldcg(fu + w);
-          if (!f) continue;
-          const uint32_t lo = j0 > (w << 5) ? j0 : (w << 5);
-          const uint32_t hi = j1 < (w << 5) + 32 ? j1 : (w << 5) + 32;
-          uint32_t live = 0;
-          for (uint32_t j = lo; j < hi; ++j) {
-            bool l;
-            if (a.mask) l = a.mask[(uint64_t)e * a.R + j] != 0;
-            else l = lane_live(__ldg(a.Xs + j), h, a.T32, a.all_live);
-            live |= (uint32_t)l << (j & 31);
+      // u's frontier row: word w sits in lane w & 31, register w >> 5
+      uint32_t r0 = 0, r1 = 0;
+      if (row_in_regs) {
+        if ((uint32_t)lane < W) r0 = __ldcg(fu + lane);
+        if ((uint32_t)lane + 32 < W) r1 = __ldcg(fu + lane + 32);
+      }
+      const int32_t beg = a.xadj[u], end = a.xadj[u + 1];
+      const int32_t e = beg + (int32_t)(ch << 5) + lane;
+      int32_t v = -1;
+      uint32_t j0 = 0, j1 = 0, h = 0;
+      if (e < end) {
+        v = a.adj[e];
+        if (v != u) {
+          if (a.mask) {
+            j1 = a.R;
+          } else {
+            h = edge_hash(u, v);
+            const uint32_t b = lane_bucket(h, a.nb);
+            j0 = __ldg(a.boff + b);
+            j1 = __ldg(a.boff + b + 1);
           }
-          uint32_t nb = f & live;
-          if (!nb) continue;
-          const uint64_t o = (uint64_t)v * W + w;
-          nb &= ~__ldcg(a.V + o);
-          if (!nb) continue;
-          const uint32_t old = atomicOr(a.V + o, nb);
-          const uint32_t gained = nb & ~old;
-          if (!gained) continue;
-          atomicOr(Fn + o, gained);
-          local += __popc(gained);
-          if (atomicCAS(a.inlist + v, 0u, 1u) == 0u) Ln[atomicAdd(a.cnt + (par ^ 1), 1u)] = v;
         }
+      }
+      const uint32_t w0 = j0 >> 5;
+      const uint32_t nw = j1 > j0 ? ((j1 - 1) >> 5) - w0 + 1 : 0u;
+      uint32_t maxw = nw;
+#pragma unroll
+      for (int d = 16; d > 0; d >>= 1) {
+        const uint32_t o = __shfl_xor_sync(kFull, maxw, d);
+        maxw = o > maxw ? o : maxw;
+      }
+      for (uint32_t k = 0; k < maxw; ++k) {
+        const uint32_t w = w0 + k;
+        uint32_t f;
+        if (row_in_regs) {
+          const uint32_t src = w & 31u;
+          const uint32_t x0 = __shfl_sync(kFull, r0, src);
+          const uint32_t x1 = __shfl_sync(kFull, r1, src);
+          f = (w >> 5) ? x1 : x0;
+        } else {
+          f = k < nw ? __ldcg(fu + w) : 0u;
+        }
+        if (k >= nw) continue;
+        f &= lane_range_mask(w, j0, j1);
+        uint32_t nbits = 0;
+        while (f) {  // test only the frontier lanes of this word
+          const int bit = __ffs(f) - 1;
+          f &= f - 1;
+          const uint32_t j = (w << 5) + (uint32_t)bit;
+          bool l;
+          if (a.mask) l = a.mask[(uint64_t)e * a.R + j] != 0;
+          else l = lane_live(__ldg(a.Xs + j), h, a.T32, a.all_live);
+          nbits |= (uint32_t)l << bit;
+        }
+        if (!nbits) continue;
+        const uint64_t o = (uint64_t)v * W + w;
+        const uint32_t old = atomicOr(a.V + o, nbits);
+        const uint32_t gained = nbits & ~old;
+        if (!gained) continue;
+        atomicOr(Fn + o, gained);
+        local += __popc(gained);
+        if (atomicMax(a.stamp + v, next_stamp) < next_stamp) push_frontier(a, v, level + 1, Ln, Qn);
       }
     }
     grid.sync();
-    const uint32_t cn = __ldcg(a.cnt + (par ^ 1));
-    for (uint64_t i = tid; i < (uint64_t)cc * W; i += nthr)
-      Fc[(uint64_t)Lc[i / W] * W + (i % W)] = 0u;
-    for (uint64_t i = tid; i < cn; i += nthr) a.inlist[Ln[i]] = 0u;
-    if (tid == 0) a.cnt[par] = 0u;
-    grid.sync();
-    int32_t *tl = Lc;
-    Lc = Ln;
-    Ln = tl;
-    uint32_t *tf = Fc;
-    Fc = Fn;
-    Fn = tf;
-    par ^= 1;
   }
-  if (level > a.n + 1 && tid == 0) set_status(a.status, IM_ETIMEOUT);
+  if (level >= a.n + 2 && tid == 0) set_status(a.status, IM_ETIMEOUT);
 #pragma unroll
   for (int d = 16; d > 0; d >>= 1) local += __shfl_xor_sync(kFull, local, d);
   if (lane == 0 && local) atomicAdd(a.acc, local);
   grid.sync();
-  if (tid == 0) *a.out = (uint64_t)__ldcg(a.acc);
+  if (tid == 0) {
+    *a.out = (uint64_t)__ldcg(a.acc);
+    if (a.stats) atomicAdd(a.stats + 3, (unsigned long long)level);
+  }
 }
 
 cudaError_t launch_spread(const im_graph *g, const im_workspace *ws, const QueryParams &q,
@@ -171,15 +237,22 @@ cudaError_t launch_spread(const im_graph *g, const im_workspace *ws, const Query
   a.seeds = d_seeds;
   a.num_seeds = num_seeds;
   a.V = ws->d_V;
-  a.F0 = ws->d_F0;
-  a.F1 = ws->d_F1;
-  a.L0 = ws->d_L0;
-  a.L1 = ws->d_L1;
-  a.inlist = ws->d_inlist;
-  a.cnt = ws->d_cnt;
+  a.F[0] = ws->d_F0;
+  a.F[1] = ws->d_F1;
+  a.F[2] = ws->d_F2;
+  a.L[0] = ws->d_L0;
+  a.L[1] = ws->d_L1;
+  a.L[2] = ws->d_L2;
+  a.Q[0] = ws->d_Q0;
+  a.Q[1] = ws->d_Q1;
+  a.Q[2] = ws->d_Q2;
+  a.stamp = ws->d_inlist;
+  a.cntlev = ws->d_cnt;
+  a.chklev = ws->d_cnt + (g->n + 4);
   a.acc = ws->d_acc;
   a.out = d_sigma;
   a.status = ws->d_status;
+  a.stats = ws->d_stats;
   int per_sm = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spread, 512, 0);
   if (e != cudaSuccess) return e;

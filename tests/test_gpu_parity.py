@@ -116,10 +116,10 @@ def test_isolated_vertices_self_loops_duplicates_unsorted():
     n = 60
     rng = np.random.default_rng(8)
     e = [(int(a), int(b)) for a, b in rng.integers(0, 40, size=(120, 2))]  # 40..59 isolated
-    e += [(5, 5), (7, 7)]  # self-loops
+    e += [(5, 5), (7, 7)]  # self-loops (both orientations: two arcs u->u)
     e += e[:10]  # duplicates
-    u = np.array([a for a, b in e] + [b for a, b in e if a != b])
-    v = np.array([b for a, b in e] + [a for a, b in e if a != b])
+    u = np.array([a for a, b in e] + [b for a, b in e])
+    v = np.array([b for a, b in e] + [a for a, b in e])
     order = rng.permutation(len(u))  # unsorted neighbour lists
     u, v = u[order], v[order]
     idx = np.argsort(u, kind="stable")
