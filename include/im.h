@@ -94,6 +94,32 @@ int im_select_seeds(const im_graph *g, int32_t K, int32_t R, double p, uint32_t 
 int im_estimate_spread(const im_graph *g, const int32_t *seeds, int32_t num_seeds, int32_t R,
                        double p, uint32_t rng_seed, uint64_t *out_sigma_R);
 
+/* Limits of im_estimate_spread_noalloc (the size of its static scratch). */
+#define IM_NOALLOC_MAX_N 32768      /* vertices; also the largest num_seeds */
+#define IM_NOALLOC_MAX_EDGES 524288 /* undirected edges m */
+#define IM_NOALLOC_MAX_R 256        /* samples */
+
+/* The same result as im_estimate_spread, computed without allocating any
+ * device memory during the call. The paper has no counterpart: this is an
+ * interface of this library, for callers that must not allocate, such as code
+ * that runs while another allocator (a framework's caching pool) holds nearly
+ * all free device memory, so that cudaMalloc would fail, or a latency-bound
+ * loop in which cudaFree would synchronize the whole device.
+ * All device scratch lives in one static region of the library's device code
+ * (about 6.4 MiB, reserved when that code is loaded on a device), so inputs
+ * are capped: g->n <= IM_NOALLOC_MAX_N, m <= IM_NOALLOC_MAX_EDGES,
+ * R <= IM_NOALLOC_MAX_R, num_seeds <= IM_NOALLOC_MAX_N. Larger inputs return
+ * IM_EINVAL before any device work.
+ * The first call on a device looks the region up (which may load the
+ * library's device code); make that first call before any stream capture.
+ * Every call on a device uses the same region: calls that overlap in time, for
+ * example from two host threads, race on it and return wrong results.
+ * seeds is a host array of num_seeds ids (duplicates count once);
+ * *out_sigma_R is written on the host. Runs on the thread's stream; blocking.
+ * Errors: IM_EINVAL (limits, R, p, seed ids, null arguments), IM_ECUDA. */
+int im_estimate_spread_noalloc(const im_graph *g, const int32_t *seeds, int32_t num_seeds,
+                               int32_t R, double p, uint32_t rng_seed, uint64_t *out_sigma_R);
+
 /* ---------------------------------------------------------------- async API */
 
 /* Device scratch for queries with R <= R_max on graph g (about

@@ -57,6 +57,7 @@ def lib():
         "im_graph_info": [P, P, P],
         "im_select_seeds": [P, i32, i32, f64, u32, P, P],
         "im_estimate_spread": [P, P, i32, i32, f64, u32, P],
+        "im_estimate_spread_noalloc": [P, P, i32, i32, f64, u32, P],
         "im_workspace_create": [P, i32, P],
         "im_workspace_destroy": [P],
         "im_select_seeds_async": [P, P, i32, i32, f64, u32, P, P],
@@ -200,6 +201,26 @@ def im_estimate_spread(g, seeds, R, p, rng_seed):
     _check(lib().im_estimate_spread(_gh(g), _ptr(seeds), seeds.shape[0], R, p,
                                     rng_seed & 0xFFFFFFFF, ctypes.byref(out)))
     return int(out.value)
+
+
+def im_estimate_spread_noalloc(g, seeds, R, p, rng_seed):
+    """im_estimate_spread without device allocation (static scratch; see
+    NOALLOC_LIMITS for the largest n, m, R and seed count it accepts)."""
+    seeds = np.ascontiguousarray(seeds, dtype=np.int32)
+    out = ctypes.c_uint64()
+    _check(lib().im_estimate_spread_noalloc(_gh(g), _ptr(seeds), seeds.shape[0], R, p,
+                                            rng_seed & 0xFFFFFFFF, ctypes.byref(out)))
+    return int(out.value)
+
+
+def _header_defines(prefix):
+    with open(HEADER) as f:
+        text = f.read()
+    return {k: int(v) for k, v in re.findall(r"^#define\s+(%s\w+)\s+(\d+)" % prefix, text, re.M)}
+
+
+# Limits of im_estimate_spread_noalloc, read from include/im.h.
+NOALLOC_LIMITS = _header_defines("IM_NOALLOC_")
 
 
 def im_workspace_create(g, R_max):

@@ -14,6 +14,48 @@
 
 using namespace imgb;
 
+// ------------------------------------------------------------------ static scratch
+// Device scratch of im_estimate_spread_noalloc, sized for the IM_NOALLOC_*
+// limits: the lane tables of the spread prologue and every buffer of the
+// spread kernel, each at a 256-byte-aligned offset (NoallocLayout below).
+namespace {
+constexpr size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+struct NoallocLayout {
+  static constexpr size_t kN = IM_NOALLOC_MAX_N;
+  static constexpr size_t kR = IM_NOALLOC_MAX_R;
+  static constexpr size_t kW = (kR + 31) / 32;                // bitset words per vertex
+  static constexpr size_t kQ = kN + IM_NOALLOC_MAX_EDGES / 16 + 1;  // work chunks per level
+  static constexpr size_t X = 0;
+  static constexpr size_t Xs = X + align256(4 * kR);
+  static constexpr size_t perm = Xs + align256(4 * kR);
+  static constexpr size_t boff = perm + align256(4 * kR);
+  static constexpr size_t sortbuf = boff + align256(4 * ((1u << kMaxBucketBits) + 1));
+  static constexpr size_t keyrange = sortbuf + align256(4);
+  static constexpr size_t V = keyrange + align256(16);
+  static constexpr size_t F0 = V + align256(4 * kN * kW);
+  static constexpr size_t F1 = F0 + align256(4 * kN * kW);
+  static constexpr size_t F2 = F1 + align256(4 * kN * kW);
+  static constexpr size_t L0 = F2 + align256(4 * kN * kW);
+  static constexpr size_t L1 = L0 + align256(4 * kN);
+  static constexpr size_t L2 = L1 + align256(4 * kN);
+  static constexpr size_t Q0 = L2 + align256(4 * kN);
+  static constexpr size_t Q1 = Q0 + align256(8 * kQ);
+  static constexpr size_t Q2 = Q1 + align256(8 * kQ);
+  static constexpr size_t stamp = Q2 + align256(8 * kQ);
+  static constexpr size_t cnt = stamp + align256(4 * kN);
+  static constexpr size_t acc = cnt + align256(4 * 2 * (kN + 4));
+  static constexpr size_t stats = acc + align256(8);
+  static constexpr size_t status = stats + align256(8 * IM_NUM_STATS);
+  static constexpr size_t seeds = status + align256(4);
+  static constexpr size_t sigma = seeds + align256(4 * kN);
+  static constexpr size_t bytes = sigma + align256(8);
+};
+static_assert(NoallocLayout::kR <= (size_t)kSortSmemMax, "lane sort must stay in shared memory");
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NoallocLayout::bytes];
+
 namespace {
 
 thread_local std::string t_err;
@@ -293,6 +335,65 @@ int ensure_seed_in(im_workspace *ws, int64_t count) {
 
 }  // namespace
 
+namespace {
+
+// Device address of g_noalloc_scratch per device, looked up once (with that
+// device current) by the first im_estimate_spread_noalloc call on it.
+constexpr int kNoallocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+unsigned char *g_noalloc_base[kNoallocMaxDevices] = {};
+
+int noalloc_base(int device, unsigned char **out) {
+  if (device < 0 || device >= kNoallocMaxDevices)
+    return fail(IM_EINVAL, "device %d outside the no-alloc table", device);
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_base[device]) {
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress of the no-alloc scratch");
+    g_noalloc_base[device] = static_cast<unsigned char *>(p);
+  }
+  *out = g_noalloc_base[device];
+  return IM_OK;
+}
+
+// A workspace whose spread buffers all point into the static scratch; only
+// the fields the spread prologue and kernel read are set.
+im_workspace noalloc_workspace(const im_graph *g, int32_t R, unsigned char *b) {
+  using L = NoallocLayout;
+  im_workspace ws;
+  ws.g = g;
+  ws.device = g->device;
+  ws.R_max = R;
+  ws.d_X = reinterpret_cast<uint32_t *>(b + L::X);
+  ws.d_Xs = reinterpret_cast<uint32_t *>(b + L::Xs);
+  ws.d_perm = reinterpret_cast<uint32_t *>(b + L::perm);
+  ws.d_boff = reinterpret_cast<uint32_t *>(b + L::boff);
+  ws.d_sortbuf = reinterpret_cast<uint32_t *>(b + L::sortbuf);
+  ws.d_keyrange = reinterpret_cast<uint64_t *>(b + L::keyrange);
+  ws.d_V = reinterpret_cast<uint32_t *>(b + L::V);
+  ws.d_F0 = reinterpret_cast<uint32_t *>(b + L::F0);
+  ws.d_F1 = reinterpret_cast<uint32_t *>(b + L::F1);
+  ws.d_F2 = reinterpret_cast<uint32_t *>(b + L::F2);
+  ws.d_L0 = reinterpret_cast<int32_t *>(b + L::L0);
+  ws.d_L1 = reinterpret_cast<int32_t *>(b + L::L1);
+  ws.d_L2 = reinterpret_cast<int32_t *>(b + L::L2);
+  ws.d_Q0 = reinterpret_cast<uint64_t *>(b + L::Q0);
+  ws.d_Q1 = reinterpret_cast<uint64_t *>(b + L::Q1);
+  ws.d_Q2 = reinterpret_cast<uint64_t *>(b + L::Q2);
+  ws.d_inlist = reinterpret_cast<uint32_t *>(b + L::stamp);
+  ws.d_cnt = reinterpret_cast<uint32_t *>(b + L::cnt);
+  ws.d_acc = reinterpret_cast<unsigned long long *>(b + L::acc);
+  ws.d_stats = reinterpret_cast<unsigned long long *>(b + L::stats);
+  ws.d_status = reinterpret_cast<int32_t *>(b + L::status);
+  ws.d_seeds_in = reinterpret_cast<int32_t *>(b + L::seeds);
+  ws.seed_in_cap = (int64_t)L::kN;
+  ws.d_sigma_out = reinterpret_cast<uint64_t *>(b + L::sigma);
+  return ws;
+}
+
+}  // namespace
+
 extern "C" {
 
 const char *im_last_error(void) { return t_err.c_str(); }
@@ -518,6 +619,46 @@ int im_estimate_spread(const im_graph *g_, const int32_t *seeds, int32_t num_see
   API_CUDA(cudaMemcpyAsync(out_sigma_R, ws->d_sigma_out, sizeof(uint64_t),
                            cudaMemcpyDeviceToHost, s), "copy sigma");
   return take_status(ws, s);
+}
+
+// Same kernels and launches as im_estimate_spread; every device buffer is a
+// slice of g_noalloc_scratch, so nothing is allocated or freed here.
+int im_estimate_spread_noalloc(const im_graph *g, const int32_t *seeds, int32_t num_seeds,
+                               int32_t R, double p, uint32_t rng_seed, uint64_t *out_sigma_R) {
+  if (!g) return fail(IM_EINVAL, "null graph");
+  if (num_seeds < 0) return fail(IM_EINVAL, "num_seeds < 0");
+  if (!out_sigma_R || (num_seeds > 0 && !seeds)) return fail(IM_EINVAL, "null argument");
+  if (g->n > IM_NOALLOC_MAX_N)
+    return fail(IM_EINVAL, "n=%d exceeds IM_NOALLOC_MAX_N=%d", g->n, IM_NOALLOC_MAX_N);
+  if (g->m > IM_NOALLOC_MAX_EDGES)
+    return fail(IM_EINVAL, "m=%lld exceeds IM_NOALLOC_MAX_EDGES=%d", (long long)g->m,
+                IM_NOALLOC_MAX_EDGES);
+  if (R > IM_NOALLOC_MAX_R)
+    return fail(IM_EINVAL, "R=%d exceeds IM_NOALLOC_MAX_R=%d", R, IM_NOALLOC_MAX_R);
+  if (num_seeds > IM_NOALLOC_MAX_N)
+    return fail(IM_EINVAL, "num_seeds=%d exceeds IM_NOALLOC_MAX_N=%d", num_seeds, IM_NOALLOC_MAX_N);
+  for (int32_t i = 0; i < num_seeds; ++i)
+    if (seeds[i] < 0 || seeds[i] >= g->n) return fail(IM_EINVAL, "seed id %d out of range", seeds[i]);
+  QueryParams q;
+  int rc = make_params(g, R, p, rng_seed, &q);
+  if (rc != IM_OK) return rc;
+  DeviceGuard dg(g->device);
+  unsigned char *base = nullptr;
+  rc = noalloc_base(g->device, &base);
+  if (rc != IM_OK) return rc;
+  const im_workspace ws = noalloc_workspace(g, R, base);
+  cudaStream_t s = t_stream;
+  // The status word must start at zero; the spread kernel clears its own
+  // frontier, visited and counter buffers.
+  API_CUDA(cudaMemsetAsync(ws.d_status, 0, sizeof(int32_t), s), "clear status");
+  if (num_seeds > 0)
+    API_CUDA(cudaMemcpyAsync(ws.d_seeds_in, seeds, sizeof(int32_t) * num_seeds,
+                             cudaMemcpyHostToDevice, s), "copy seeds");
+  rc = enqueue_spread(g, &ws, ws.d_seeds_in, num_seeds, q, nullptr, ws.d_sigma_out, s);
+  if (rc != IM_OK) return rc;
+  API_CUDA(cudaMemcpyAsync(out_sigma_R, ws.d_sigma_out, sizeof(uint64_t),
+                           cudaMemcpyDeviceToHost, s), "copy sigma");
+  return take_status(&ws, s);
 }
 
 // ------------------------------------------------------------------ test hooks
