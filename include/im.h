@@ -221,6 +221,15 @@ uint64_t im_kernel_launches(void);
 int im_debug_labels(const im_graph *g, int32_t R, double p, uint32_t rng_seed,
                     int32_t *out_labels);
 
+/* Labels and size memo of selected simulations only (for full-size graphs
+ * whose whole table is too large to copy): lanes[k] in [0, R) are simulation
+ * indices; out_labels[v*num_lanes + k] is the label of v in simulation
+ * lanes[k] and out_sizes[v*num_lanes + k] the size of the component rooted at
+ * v there (0 if v is not a root). Host arrays of n*num_lanes entries. */
+int im_debug_tables_lanes(const im_graph *g, int32_t R, double p, uint32_t rng_seed,
+                          const int32_t *lanes, int32_t num_lanes, int32_t *out_labels,
+                          uint32_t *out_sizes);
+
 /* Size memo (Section 3.3): out[l*R + r] = #{v : label of v in sample r is l},
  * zero where l is not a component label of sample r. */
 int im_debug_sizes(const im_graph *g, int32_t R, double p, uint32_t rng_seed,

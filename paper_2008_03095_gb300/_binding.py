@@ -68,6 +68,7 @@ def lib():
         "im_sampling_threshold": [f64, P],
         "im_debug_labels": [P, i32, f64, u32, P],
         "im_debug_sizes": [P, i32, f64, u32, P],
+        "im_debug_tables_lanes": [P, i32, f64, u32, P, i32, P, P],
         "im_debug_lane_randoms": [i32, u32, P],
         "im_debug_edge_hash": [P, P, i64, P],
         "im_debug_select_seeds_masked": [P, i32, i32, P, P, P, P, P],
@@ -299,6 +300,17 @@ def im_debug_labels(g, R, p, rng_seed):
     out = np.empty((g.n, R), dtype=np.int32)
     _check(lib().im_debug_labels(_gh(g), R, p, rng_seed & 0xFFFFFFFF, _ptr(out)))
     return out
+
+
+def im_debug_tables_lanes(g, R, p, rng_seed, lanes):
+    """(labels int32[n, L], sizes uint32[n, L]) for the simulations in `lanes`."""
+    lanes = np.ascontiguousarray(lanes, dtype=np.int32)
+    n = g.n
+    lab = np.empty((n, lanes.shape[0]), dtype=np.int32)
+    siz = np.empty((n, lanes.shape[0]), dtype=np.uint32)
+    _check(lib().im_debug_tables_lanes(_gh(g), R, p, rng_seed & 0xFFFFFFFF, _ptr(lanes),
+                                       lanes.shape[0], _ptr(lab), _ptr(siz)))
+    return lab, siz
 
 
 def im_debug_sizes(g, R, p, rng_seed):

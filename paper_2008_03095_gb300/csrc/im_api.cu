@@ -715,6 +715,54 @@ int im_debug_labels(const im_graph *g, int32_t R, double p, uint32_t rng_seed,
   return debug_tables(g, R, p, rng_seed, nullptr, out_labels, nullptr);
 }
 
+int im_debug_tables_lanes(const im_graph *g_, int32_t R, double p, uint32_t rng_seed,
+                          const int32_t *lanes, int32_t num_lanes, int32_t *out_labels,
+                          uint32_t *out_sizes) {
+  if (!g_) return fail(IM_EINVAL, "null graph");
+  if (num_lanes < 1 || !lanes || !out_labels || !out_sizes) return fail(IM_EINVAL, "null argument");
+  for (int32_t k = 0; k < num_lanes; ++k)
+    if (lanes[k] < 0 || lanes[k] >= R) return fail(IM_EINVAL, "simulation %d outside [0, R)", lanes[k]);
+  im_graph *g = const_cast<im_graph *>(g_);
+  QueryParams q;
+  int rc = make_params(g, R, p, rng_seed, &q);
+  if (rc != IM_OK) return rc;
+  std::lock_guard<std::mutex> lock(g->mu);
+  DeviceGuard dg(g->device);
+  im_workspace *ws = nullptr;
+  rc = internal_ws(g, R, &ws);
+  if (rc != IM_OK) return rc;
+  cudaStream_t s = t_stream;
+  rc = enqueue_select(g, ws, 0, q, nullptr, nullptr, nullptr, s, true);
+  if (rc != IM_OK) return rc;
+  // internal lane of each requested simulation index (perm: lane -> simulation)
+  std::vector<uint32_t> perm(R), inv(R), sel(num_lanes);
+  API_CUDA(cudaMemcpyAsync(perm.data(), ws->d_perm, sizeof(uint32_t) * R, cudaMemcpyDeviceToHost, s),
+           "copy lane order");
+  API_CUDA(cudaStreamSynchronize(s), "stream synchronize");
+  for (int32_t j = 0; j < R; ++j) inv[perm[j]] = (uint32_t)j;
+  for (int32_t k = 0; k < num_lanes; ++k) sel[k] = inv[lanes[k]];
+  const size_t cnt = (size_t)g->n * num_lanes;
+  uint32_t *d_sel = nullptr;
+  int32_t *d_lab = nullptr;
+  uint32_t *d_siz = nullptr;
+  cudaError_t e = dalloc(&d_sel, (size_t)num_lanes);
+  if (e == cudaSuccess) e = dalloc(&d_lab, cnt);
+  if (e == cudaSuccess) e = dalloc(&d_siz, cnt);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d_sel, sel.data(), sizeof(uint32_t) * num_lanes, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = launch_gather_lanes(g, ws, q, d_sel, (uint32_t)num_lanes, d_lab, d_siz, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(out_labels, d_lab, sizeof(int32_t) * cnt, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(out_sizes, d_siz, sizeof(uint32_t) * cnt, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (d_sel) cudaFree(d_sel);
+  if (d_lab) cudaFree(d_lab);
+  if (d_siz) cudaFree(d_siz);
+  if (e != cudaSuccess) return cuda_fail(e, "debug tables on selected simulations");
+  return take_status(ws, s);
+}
+
 int im_debug_sizes(const im_graph *g, int32_t R, double p, uint32_t rng_seed,
                    uint32_t *out_sizes) {
   if (!out_sizes) return fail(IM_EINVAL, "null output");

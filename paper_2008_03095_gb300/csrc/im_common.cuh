@@ -196,6 +196,9 @@ cudaError_t launch_gains(const im_graph *g, const im_workspace *ws, const QueryP
                          cudaStream_t s);
 cudaError_t launch_expand(const im_graph *g, const im_workspace *ws, const QueryParams &q,
                           int32_t *d_labels, uint32_t *d_sizes, cudaStream_t s);
+cudaError_t launch_gather_lanes(const im_graph *g, const im_workspace *ws, const QueryParams &q,
+                                const uint32_t *d_lanes, uint32_t nl, int32_t *d_labels,
+                                uint32_t *d_sizes, cudaStream_t s);
 cudaError_t launch_edge_hash(const int32_t *d_u, const int32_t *d_v, int64_t count,
                              uint32_t *d_h, cudaStream_t s);
 cudaError_t launch_celf(const im_graph *g, const im_workspace *ws, const QueryParams &q, int K,

@@ -440,6 +440,28 @@ cudaError_t launch_expand(const im_graph *g, const im_workspace *ws, const Query
   return cudaGetLastError();
 }
 
+// Selected simulations only: lanes[k] is the internal lane of the k-th
+// requested simulation; out[v*nl + k] in the layout of the size memo.
+__global__ void k_gather_lanes(const int32_t *P, const uint32_t *lanes, uint32_t n, uint32_t R,
+                               uint32_t nl, int32_t *labels, uint32_t *sizes) {
+  const uint64_t total = (uint64_t)n * nl;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t v = (uint32_t)(i / nl), k = (uint32_t)(i % nl);
+    const int32_t x = P[(uint64_t)v * R + lanes[k]];
+    labels[i] = x < 0 ? (int32_t)v : x;
+    sizes[i] = x < 0 ? (uint32_t)(-x) : 0u;
+  }
+}
+
+cudaError_t launch_gather_lanes(const im_graph *g, const im_workspace *ws, const QueryParams &q,
+                                const uint32_t *d_lanes, uint32_t nl, int32_t *d_labels,
+                                uint32_t *d_sizes, cudaStream_t s) {
+  k_gather_lanes<<<g->num_sms * 4, 256, 0, s>>>(ws->d_P, d_lanes, (uint32_t)g->n, q.R, nl,
+                                                d_labels, d_sizes);
+  return cudaGetLastError();
+}
+
 __global__ void k_edge_hash(const int32_t *u, const int32_t *v, int64_t count, uint32_t *h) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
        i += (int64_t)gridDim.x * blockDim.x)

@@ -1,0 +1,121 @@
+"""Parity at the full workload sizes, in the launch configuration bench.py
+times (a workspace per graph, im_select_seeds_async + im_estimate_spread_async
+on one stream).
+
+- powerlaw_n37154 (n = 37,154, R = 2048): the whole seed sequence and sigma*R
+  equal the oracle's; labels and sizes of sampled simulations too.
+- clustered_n334863 and powerlaw_n4m (label tables of 2.7 and 8.2 GB): labels
+  and sizes of sampled simulations equal the oracle's bit for bit, and the
+  selection satisfies properties that hold at any size, checked with the spread
+  kernel, which shares no code with the lazy greedy:
+    * sigma*R of every checked prefix equals the spread estimate of that prefix;
+    * the first seed's gain equals the spread of the first seed alone;
+    * at checked steps no sampled competitor has a larger marginal gain, and on
+      equal gain the chosen id is the lower one (greedy with lowest-id ties).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2008_03095_gb300 as im
+from paper_2008_03095_gb300 import build as im_build
+from paper_2008_03095_gb300 import synth
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    im_build.build()
+    im.lib()
+
+
+def _select_like_bench(g, w, p):
+    import torch
+
+    R, K, seed = w["R"], w["K"], w["rng_seed"]
+    dev = torch.device("cuda", 0)
+    im.im_set_stream(torch.cuda.current_stream())
+    ws = im.im_workspace_create(g, R)
+    d_seeds = torch.empty(K, dtype=torch.int32, device=dev)
+    d_sigma = torch.empty(K, dtype=torch.int64, device=dev)
+    d_spread = torch.empty(1, dtype=torch.int64, device=dev)
+    im.im_select_seeds_async(g, ws, K, R, p, seed, d_seeds, d_sigma)
+    im.im_estimate_spread_async(g, ws, d_seeds, K, R, p, seed, d_spread)
+    im.im_workspace_status(ws)
+    seeds = d_seeds.cpu().numpy()
+    sigma = d_sigma.cpu().numpy().astype(np.uint64)
+    spread = int(d_spread.cpu().numpy()[0])
+    ws.close()
+    im.im_set_stream(None)
+    return seeds, sigma, spread
+
+
+def _sampled_lanes_match(g, xadj, adj, w, p, lanes):
+    R, seed = w["R"], w["rng_seed"]
+    glab, gsiz = im.im_debug_tables_lanes(g, R, p, seed, lanes)
+    olab, osiz = oracle.labels_lanes(xadj, adj, R, p, seed, lanes)
+    assert np.array_equal(glab, olab)
+    assert np.array_equal(gsiz, osiz)
+
+
+def _greedy_properties(g, xadj, w, p, seeds, sigma, spread, rng):
+    R, K, seed = w["R"], w["K"], w["rng_seed"]
+    n = xadj.shape[0] - 1
+    assert len(set(seeds.tolist())) == K and seeds.min() >= 0 and seeds.max() < n
+    assert np.all(np.diff(sigma.astype(np.int64)) >= 0)
+    assert spread == int(sigma[-1])
+    for k in (0, 1, K // 2, K - 1):
+        assert im.im_estimate_spread(g, seeds[:k + 1], R, p, seed) == int(sigma[k])
+    deg = np.diff(xadj)
+    top = np.argsort(-deg, kind="stable")[:6]
+    for k in (0, 1, K - 1):
+        base = int(sigma[k - 1]) if k > 0 else 0
+        gain = int(sigma[k]) - base
+        cands = np.concatenate([top, rng.integers(0, n, size=6)])
+        for u in cands:
+            if u in seeds[:k + 1]:
+                continue
+            gu = im.im_estimate_spread(g, np.append(seeds[:k], u), R, p, seed) - base
+            assert gu <= gain, (k, int(u), gu, gain)
+            if gu == gain:
+                assert seeds[k] < u
+
+
+@pytest.mark.parametrize("p", [0.01, 0.05])
+def test_powerlaw_n37154_full_parity(p):
+    name = "powerlaw_n37154"
+    w = synth.WORKLOADS[name]
+    xadj, adj = synth.workload_graph(name)
+    g = im.im_graph_create(xadj, adj)
+    seeds, sigma, spread = _select_like_bench(g, w, p)
+    oseeds, osigma = oracle.select_seeds(xadj, adj, w["K"], w["R"], p, w["rng_seed"])
+    assert np.array_equal(seeds, oseeds)
+    assert np.array_equal(sigma, osigma)
+    assert spread == int(osigma[-1])
+    _sampled_lanes_match(g, xadj, adj, w, p, [0, 1, 1023, 2047])
+    g.close()
+
+
+@pytest.mark.parametrize("p", [0.01, 0.05])
+def test_clustered_n334863_sampled_parity_and_greedy_properties(p):
+    name = "clustered_n334863"
+    w = synth.WORKLOADS[name]
+    xadj, adj = synth.workload_graph(name)
+    g = im.im_graph_create(xadj, adj)
+    _sampled_lanes_match(g, xadj, adj, w, p, [0, 5, 1500, 2047])
+    seeds, sigma, spread = _select_like_bench(g, w, p)
+    _greedy_properties(g, xadj, w, p, seeds, sigma, spread, np.random.default_rng(4))
+    g.close()
+
+
+def test_powerlaw_n4m_sampled_parity_and_greedy_properties():
+    name = "powerlaw_n4m"
+    w = synth.WORKLOADS[name]
+    xadj, adj = synth.workload_graph(name)
+    g = im.im_graph_create(xadj, adj)
+    p = w["ps"][0]
+    _sampled_lanes_match(g, xadj, adj, w, p, [0, 511])
+    seeds, sigma, spread = _select_like_bench(g, w, p)
+    _greedy_properties(g, xadj, w, p, seeds, sigma, spread, np.random.default_rng(41))
+    g.close()
