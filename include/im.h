@@ -158,10 +158,10 @@ enum {
   IM_STAT_CELF_CYC_COMMIT = 6,   /* ... in commits and pool updates */
   IM_STAT_CELF_CYC_MERGE = 7,    /* ... in merging survivors back */
   IM_STAT_CELF_REFRESHES = 8,    /* grid-wide recomputations of all exact gains */
-  IM_STAT_CELF_CYC_PICK = 9,     /* commit loop: choosing the best pool member */
-  IM_STAT_CELF_CYC_BOOK = 10,    /* commit loop: recording the seed */
-  IM_STAT_CELF_CYC_UPDATE = 11,  /* commit loop: updating the other pool gains */
-  IM_STAT_CELF_CYC_COVER = 12,   /* marking the round's components covered */
+  IM_STAT_CELF_CYC_COMMITS = 9,  /* ... in the commit loop (picks, pool updates) */
+  IM_STAT_CELF_CYC_COVER = 10,   /* ... marking committed components covered */
+  IM_STAT_RESERVED_11 = 11,      /* 0 */
+  IM_STAT_RESERVED_12 = 12,      /* 0 */
   IM_STAT_CHECK_CODE = 13,       /* first failed internal invariant check (0 = none) */
   IM_STAT_CHECK_V0 = 14,         /* ... and two values describing it */
   IM_STAT_CHECK_V1 = 15,

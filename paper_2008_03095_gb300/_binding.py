@@ -250,8 +250,8 @@ def im_workspace_status(ws):
 
 STATS = ("celf_rounds", "celf_evaluations", "celf_extractions", "spread_levels",
          "celf_cycles_extract", "celf_cycles_eval", "celf_cycles_commit", "celf_cycles_merge",
-         "celf_refreshes", "celf_cycles_pick", "celf_cycles_book", "celf_cycles_update",
-         "celf_cycles_cover", "check_code", "check_v0", "check_v1")
+         "celf_refreshes", "celf_cycles_commits", "celf_cycles_cover", "reserved_11",
+         "reserved_12", "check_code", "check_v0", "check_v1")
 
 
 def im_workspace_stats(ws):

@@ -86,6 +86,7 @@ struct CelfArgs {
   int B;
   int pool_smem;
   uint32_t refresh_after;  // evaluations without a commit that trigger a refresh
+  uint32_t magic_R;        // ceil(2^32 / R) for div_R (0 when R == 1)
   uint32_t round_cap;      // budget of driver rounds (see launch_celf)
   uint32_t *g_pool;
   int32_t *out_seeds;
@@ -99,11 +100,11 @@ struct CelfSmem {
   uint32_t hist[kBins];
   uint64_t red[kCelfWarps];
   int32_t pid[kPoolMax];
-  uint32_t pgain[kPoolMax];
-  int32_t pactive[kPoolMax];
+  uint32_t pgain[2][kPoolMax];   // exact gains of the pool, double-buffered by commit
+  int32_t pactive[2][kPoolMax];  // pool member still a candidate, same buffering
   int32_t committed[kPoolMax];
   uint64_t Y[kPoolMax];
-  uint32_t ny, ncommit;
+  uint32_t ny;
   uint64_t sel_t, sel_A, sel_B;
   uint32_t sel_above;
   int sel_done;
@@ -328,7 +329,7 @@ __device__ uint64_t block_reduce_u64(uint64_t v, bool is_max, CelfSmem &s) {
   if (lane == 0) s.red[warp] = v;
   __syncthreads();
   if (warp == 0) {
-    v = s.red[lane];
+    v = lane < kCelfWarps ? s.red[lane] : (is_max ? 0ull : ~0ull);
     v = is_max ? warp_max_u64(v) : warp_min_u64(v);
     if (lane == 0) s.red[0] = v;
   }
@@ -472,11 +473,21 @@ struct Driver {
   uint64_t sig_out = 0;
   uint32_t rounds = 0, evals = 0, evals_since_commit = 0;
   unsigned long long cyc[4] = {0, 0, 0, 0};
+  unsigned long long fine[2] = {0, 0};  // commit loop, cover atomics
 };
 
 // Block 0: lazy-greedy rounds over the prefix in shared memory until the
 // query is done or a grid step is needed. Returns the next command. POOL_SMEM:
 // the per-lane pool arrays live in shared memory (else in global memory).
+// i / R for i < 2^21 by a multiply-high with M = ceil(2^32 / R) and one
+// correction step (M = 0 encodes R = 1).
+__device__ __forceinline__ uint32_t div_R(uint32_t i, uint32_t R, uint32_t M) {
+  if (M == 0) return i;
+  uint32_t c = __umulhi(i, M);
+  if (c * R > i) --c;
+  return c;
+}
+
 template <bool POOL_SMEM>
 __device__ __noinline__ int drive_rounds(const CelfArgs &a, CelfSmem &s, uint32_t *proot, uint32_t *pcont,
                             Driver &d) {
@@ -499,9 +510,8 @@ __device__ __noinline__ int drive_rounds(const CelfArgs &a, CelfSmem &s, uint32_
     const uint32_t np = (d.nC - d.head) < B ? (d.nC - d.head) : B;
     if (tid < (int)np) {
       s.pid[tid] = key_vertex(s.C[d.head + tid]);
-      s.pactive[tid] = 1;
+      s.pactive[0][tid] = 1;
     }
-    if (tid == 0) s.ncommit = 0;
     const uint64_t kc = d.head + np < d.nC ? s.C[d.head + np] : 0ull;
     const uint64_t top_out = umax64(kc, d.sig_out);
     d.evals += np;
@@ -510,30 +520,53 @@ __device__ __noinline__ int drive_rounds(const CelfArgs &a, CelfSmem &s, uint32_
 
     // ---------------------------------------------------------- exact gains
     // g(u | S) = sum_r [component of u in r not covered] * |C_r(u)|. All
-    // (candidate, lane) items are spread over the block; the loads of an item
-    // depend only on its label-table slot, so they overlap across items.
+    // (candidate, lane) items are spread over the block in one pass: a thread
+    // issues the label loads of four items together, then their dependent
+    // size and covered-bit gathers together.
     const uint32_t items = np * R;
-    for (uint32_t i = tid; i < items; i += blockDim.x) {
-      const uint32_t c = i / R, j = i - c * R;
-      proot[i] = (uint32_t)__ldg(a.P + (size_t)s.pid[c] * R + j);
+    for (uint32_t base = tid; base < items; base += 4 * kCelfThreads) {
+      int32_t xv[4];
+      uint32_t uv[4], jv[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const uint32_t i = base + q * kCelfThreads;
+        xv[q] = -1;
+        uv[q] = 0;
+        jv[q] = 0;
+        if (i < items) {
+          const uint32_t c = div_R(i, R, a.magic_R);
+          jv[q] = i - c * R;
+          uv[q] = (uint32_t)s.pid[c];
+          xv[q] = __ldg(a.P + (size_t)uv[q] * R + jv[q]);
+        }
+      }
+      uint32_t szv[4], cwv[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int32_t x = xv[q];
+        const uint32_t root = x < 0 ? uv[q] : (uint32_t)x;
+        const uint32_t bit = root * R + jv[q];
+        szv[q] = 0;
+        cwv[q] = 0;
+        if (base + q * kCelfThreads < items) {
+          // a singleton {u} (x == -1) is covered only if u is a seed
+          szv[q] = x < 0 ? (uint32_t)(-x) : (uint32_t)(-__ldg(a.P + (size_t)x * R + jv[q]));
+          cwv[q] = (x != -1) ? (__ldcg(a.cov + (bit >> 5)) >> (bit & 31)) & 1u : 0u;
+        }
+        uv[q] = root;
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const uint32_t i = base + q * kCelfThreads;
+        if (i < items) {
+          proot[i] = uv[q];
+          pcont[i] = cwv[q] ? 0u : szv[q];
+        }
+      }
     }
     __syncthreads();
-#pragma unroll 4
-    for (uint32_t i = tid; i < items; i += blockDim.x) {
-      const uint32_t c = i / R, j = i - c * R;
-      const uint32_t u = (uint32_t)s.pid[c];
-      const int32_t x = (int32_t)proot[i];
-      const uint32_t root = x < 0 ? u : (uint32_t)x;
-      const uint32_t bit = root * R + j;
-      // a singleton {u} (x == -1) is covered only if u is a seed
-      const uint32_t sz = x < 0 ? (uint32_t)(-x) : (uint32_t)(-__ldg(a.P + (size_t)x * R + j));
-      const uint32_t cw = (x != -1) ? __ldcg(a.cov + (bit >> 5)) : 0u;
-      proot[i] = root;
-      pcont[i] = ((cw >> (bit & 31)) & 1u) ? 0u : sz;
-    }
-    __syncthreads();
-    if ((uint32_t)warp < np) {
-      const uint32_t *cc = pcont + (size_t)warp * R;
+    for (uint32_t m = (uint32_t)warp; m < np; m += kCelfWarps) {
+      const uint32_t *cc = pcont + (size_t)m * R;
       uint32_t g = 0;
       if ((R & 3u) == 0) {
         const uint4 *c4 = reinterpret_cast<const uint4 *>(cc);
@@ -546,7 +579,7 @@ __device__ __noinline__ int drive_rounds(const CelfArgs &a, CelfSmem &s, uint32_
       }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(kFull, g, o);
-      if (lane == 0) s.pgain[warp] = g;
+      if (lane == 0) s.pgain[0][m] = g;
     }
     __syncthreads();
     {
@@ -556,73 +589,97 @@ __device__ __noinline__ int drive_rounds(const CelfArgs &a, CelfSmem &s, uint32_
     }
 
     // ---------------------------------------------------------- commits
-    uint64_t bk = 0;
+    // Every warp picks the best active pool member from buffer `cur` (all
+    // warps read the same values, so all make the same choice); warp m then
+    // writes member m's state after the commit (its gain minus the lanes it
+    // shares a component with the committed seed) into buffer cur ^ 1, and one
+    // barrier per commit publishes it. Nothing writes buffer cur while any
+    // warp may still read it.
+    uint32_t cur = 0, ncm = 0;
     for (;;) {
-      if (warp == 0) {
-        uint64_t k = 0;
-        if ((uint32_t)lane < np && s.pactive[lane]) k = make_key(s.pgain[lane], s.pid[lane]);
-        const uint64_t best = warp_max_u64(k);
-        const unsigned b = __ballot_sync(kFull, k != 0 && k == best);
-        if (lane == 0) {
-          s.best_key = best;
-          s.best_w = b ? __ffs(b) - 1 : -1;
-        }
-      }
-      __syncthreads();
-      bk = s.best_key;
-      const int bw = s.best_w;
+      uint64_t k = 0;
+      if ((uint32_t)lane < np && s.pactive[cur][lane]) k = make_key(s.pgain[cur][lane], s.pid[lane]);
+      const uint64_t bk = warp_max_u64(k);
+      const unsigned bb = __ballot_sync(kFull, k != 0 && k == bk);
       if (bk == 0 || bk < top_out) break;
+      const int bw = __ffs(bb) - 1;
+      const uint32_t gsel = s.pgain[cur][bw];
       if (tid == 0) {
-        d.sigma += s.pgain[bw];
-        a.out_seeds[d.nsel] = s.pid[bw];
-        a.out_sigma[d.nsel] = d.sigma;
-        a.chosen[s.pid[bw]] = 1;
-        s.pactive[bw] = 0;
-        s.committed[s.ncommit++] = bw;
+        const int32_t vsel = s.pid[bw];
+        a.out_seeds[d.nsel] = vsel;
+        a.out_sigma[d.nsel] = d.sigma + gsel;
+        a.chosen[vsel] = 1;
+        s.committed[ncm] = bw;
       }
+      d.sigma += gsel;
       ++d.nsel;
+      ++ncm;
       d.evals_since_commit = 0;
-      __syncthreads();
-      if (d.nsel >= a.K) break;
-      if ((uint32_t)warp < np && s.pactive[warp]) {
-        const uint32_t *rb = proot + (size_t)bw * R;
-        const uint32_t *rr = proot + (size_t)warp * R;
-        uint32_t *cc = pcont + (size_t)warp * R;
-        uint32_t dsum = 0;
-        if ((R & 3u) == 0) {
-          const uint4 *rb4 = reinterpret_cast<const uint4 *>(rb);
-          const uint4 *rr4 = reinterpret_cast<const uint4 *>(rr);
-          uint4 *cc4 = reinterpret_cast<uint4 *>(cc);
-          for (uint32_t q = lane; q < (R >> 2); q += 32) {
-            uint4 cv = cc4[q];
-            if (!(cv.x | cv.y | cv.z | cv.w)) continue;
-            const uint4 r = rr4[q], b = rb4[q];
-            bool dirty = false;
-            if (cv.x && r.x == b.x) { dsum += cv.x; cv.x = 0; dirty = true; }
-            if (cv.y && r.y == b.y) { dsum += cv.y; cv.y = 0; dirty = true; }
-            if (cv.z && r.z == b.z) { dsum += cv.z; cv.z = 0; dirty = true; }
-            if (cv.w && r.w == b.w) { dsum += cv.w; cv.w = 0; dirty = true; }
-            if (dirty) cc4[q] = cv;
-          }
-        } else {
-          for (uint32_t j = lane; j < R; j += 32) {
-            const uint32_t cv = cc[j];
-            if (cv && rr[j] == rb[j]) {
-              dsum += cv;
-              cc[j] = 0;
+      for (uint32_t m = (uint32_t)warp; m < np; m += kCelfWarps) {
+        uint32_t g = s.pgain[cur][m];
+        const int32_t act = (s.pactive[cur][m] && (int)m != bw) ? 1 : 0;
+        if (act && d.nsel < a.K) {
+          const uint32_t *rb = proot + (size_t)bw * R;
+          const uint32_t *rr = proot + (size_t)m * R;
+          uint32_t *cc = pcont + (size_t)m * R;
+          uint32_t dsum = 0;
+          if ((R & 3u) == 0) {
+            const uint4 *rb4 = reinterpret_cast<const uint4 *>(rb);
+            const uint4 *rr4 = reinterpret_cast<const uint4 *>(rr);
+            uint4 *cc4 = reinterpret_cast<uint4 *>(cc);
+            for (uint32_t q = lane; q < (R >> 2); q += 32) {
+              uint4 cv = cc4[q];
+              if (!(cv.x | cv.y | cv.z | cv.w)) continue;
+              const uint4 r = rr4[q], b = rb4[q];
+              bool dirty = false;
+              if (cv.x && r.x == b.x) { dsum += cv.x; cv.x = 0; dirty = true; }
+              if (cv.y && r.y == b.y) { dsum += cv.y; cv.y = 0; dirty = true; }
+              if (cv.z && r.z == b.z) { dsum += cv.z; cv.z = 0; dirty = true; }
+              if (cv.w && r.w == b.w) { dsum += cv.w; cv.w = 0; dirty = true; }
+              if (dirty) cc4[q] = cv;
+            }
+          } else {
+            for (uint32_t j = lane; j < R; j += 32) {
+              const uint32_t cv = cc[j];
+              if (cv && rr[j] == rb[j]) {
+                dsum += cv;
+                cc[j] = 0;
+              }
             }
           }
-        }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) dsum += __shfl_xor_sync(kFull, dsum, o);
-        if (lane == 0) s.pgain[warp] -= dsum;
+          for (int o = 16; o > 0; o >>= 1) dsum += __shfl_xor_sync(kFull, dsum, o);
+          g -= dsum;
+        }
+        if (lane == 0) {
+          s.pgain[cur ^ 1][m] = g;
+          s.pactive[cur ^ 1][m] = act;
+        }
       }
+      cur ^= 1;
       __syncthreads();
+      if (d.nsel >= a.K) break;
     }
+    const long long t_cover = clock64();
+    d.fine[0] += (unsigned long long)(t_cover - t_mark);
     // The round's seeds cover their components: the lanes whose contribution
     // is still > 0 are exactly those no earlier seed had covered.
-    {
-      const uint32_t ncm = s.ncommit;
+    if ((R & 31u) == 0) {
+      // With R a multiple of 32, lane j of an aligned group of 32 lanes owns
+      // bit j & 31 of word (root * R + j) >> 5, so the lanes of a warp that
+      // share a root set exactly the bits of their match mask: one atomic per
+      // distinct word instead of one per lane.
+      const uint32_t groups = R >> 5;
+      for (uint32_t t = (uint32_t)warp; t < ncm * groups; t += kCelfWarps) {
+        const uint32_t ci = t / groups;
+        const uint32_t c = (uint32_t)s.committed[ci];
+        const uint32_t j = (t - ci * groups) * 32 + (uint32_t)lane;
+        const uint32_t cv = pcont[(size_t)c * R + j];
+        const uint32_t word = cv ? (proot[(size_t)c * R + j] * R + j) >> 5 : 0xffffffffu;
+        const unsigned peers = __match_any_sync(kFull, word);
+        if (cv && lane == __ffs(peers) - 1) atomicOr(a.cov + word, peers);
+      }
+    } else {
       for (uint32_t i = tid; i < ncm * R; i += blockDim.x) {
         const uint32_t c = (uint32_t)s.committed[i / R], j = i % R;
         if (pcont[(size_t)c * R + j]) {
@@ -633,6 +690,7 @@ __device__ __noinline__ int drive_rounds(const CelfArgs &a, CelfSmem &s, uint32_
     }
     {
       const long long t_now = clock64();
+      d.fine[1] += (unsigned long long)(t_now - t_cover);
       d.cyc[2] += (unsigned long long)(t_now - t_mark);
       t_mark = t_now;
     }
@@ -643,8 +701,8 @@ __device__ __noinline__ int drive_rounds(const CelfArgs &a, CelfSmem &s, uint32_
 
     // ---------------------------------------------------------- merge survivors back
     if (warp == 0) {
-      const bool alive = (uint32_t)lane < np && s.pactive[lane];
-      uint64_t y = alive ? make_key(s.pgain[lane], s.pid[lane]) : 0ull;
+      const bool alive = (uint32_t)lane < np && s.pactive[cur][lane];
+      uint64_t y = alive ? make_key(s.pgain[cur][lane], s.pid[lane]) : 0ull;
 #pragma unroll
       for (int k = 2; k <= 32; k <<= 1) {  // bitonic sort across the warp, descending
 #pragma unroll
@@ -851,6 +909,8 @@ __global__ void __launch_bounds__(kCelfThreads, 1) k_celf(CelfArgs a) {
     atomicAdd(a.stats + 2, (unsigned long long)extracts);
     for (int i = 0; i < 4; ++i) atomicAdd(a.stats + 4 + i, d.cyc[i]);
     atomicAdd(a.stats + 8, (unsigned long long)refreshes);
+    atomicAdd(a.stats + 9, d.fine[0]);
+    atomicAdd(a.stats + 10, d.fine[1]);
   }
 }
 
@@ -875,6 +935,7 @@ cudaError_t launch_celf(const im_graph *g, const im_workspace *ws, const QueryPa
   uint32_t ra = (uint32_t)g->n / 64;
   if (ra < (uint32_t)(4 * a.B)) ra = (uint32_t)(4 * a.B);
   a.refresh_after = ra;
+  a.magic_R = q.R == 1 ? 0u : (uint32_t)(((1ull << 32) + q.R - 1) / q.R);
   // Every round evaluates at least one candidate, fewer than refresh_after
   // evaluations separate two commits or a commit and a refresh, and the
   // round after a refresh commits (its keys are exact); every grid step is
