@@ -315,53 +315,101 @@ cudaError_t launch_union(const im_graph *g, const im_workspace *ws, const QueryP
 }
 
 // ------------------------------------------------------------------ compress
-__device__ __forceinline__ void compress_slot(uint32_t idx, int32_t x, uint32_t R, int32_t *P,
-                                              int32_t *status, uint32_t cap) {
-  const uint32_t j = idx % R;
-  int32_t r = x;
-  uint32_t it = 0;
-  for (; it < cap; ++it) {
-    int32_t y = __ldcg(P + (uint32_t)r * R + j);
-    if (y < 0) break;
-    r = y;
-  }
-  if (it == cap) {
-    set_status(status, IM_ETIMEOUT);
-    return;
-  }
-  if (r != x) __stcg(P + idx, r);
-  atomicAdd(P + (uint32_t)r * R + j, -1);
-}
+// Size memo (Section 3.3): every non-root slot gets its root (the component
+// minimum) and each root slot accumulates -|component|. The label table is
+// processed in tiles of 32 vertices x 8 lanes: the block loads a tile with
+// sector-sized row reads, then warp w takes lane j0 + w of the 32 vertices,
+// so the parent lookups of a warp hit one lane (vertices that share a parent,
+// as in a giant component, coalesce into one request) and the root counters
+// take one atomic per distinct root per warp instead of one per slot. Root
+// slots are never written here except by those atomics.
+constexpr uint32_t kCompV = 32;  // vertices per tile (one per warp lane)
+constexpr uint32_t kCompL = 32;  // lanes per tile (four per warp of the block)
 
-__global__ void __launch_bounds__(256) k_compress(int32_t *P, uint32_t nR, uint32_t R,
+__global__ void __launch_bounds__(256) k_compress(int32_t *P, uint32_t n, uint32_t R,
                                                   int32_t *status, uint32_t cap) {
-  const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
-  const uint32_t nthr = gridDim.x * blockDim.x;
-  const uint32_t n4 = nR >> 2;
-  const int4 *p4 = reinterpret_cast<const int4 *>(P);
-  for (uint32_t i = tid; i < n4; i += nthr) {
-    int4 x = __ldcg(p4 + i);
-    if ((x.x & x.y & x.z & x.w) < 0) continue;  // four roots
-    const uint32_t b = i << 2;
-    if (x.x >= 0) compress_slot(b, x.x, R, P, status, cap);
-    if (x.y >= 0) compress_slot(b + 1, x.y, R, P, status, cap);
-    if (x.z >= 0) compress_slot(b + 2, x.z, R, P, status, cap);
-    if (x.w >= 0) compress_slot(b + 3, x.w, R, P, status, cap);
-  }
-  for (uint32_t i = (n4 << 2) + tid; i < nR; i += nthr) {
-    int32_t x = __ldcg(P + i);
-    if (x >= 0) compress_slot(i, x, R, P, status, cap);
+  __shared__ int32_t tile[kCompV][kCompL + 1];
+  const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+  const uint64_t tv = (n + kCompV - 1) / kCompV, tl = (R + kCompL - 1) / kCompL;
+  const uint64_t ntiles = tv * tl;
+  const bool vec = (R & 3u) == 0;  // rows start 16-byte aligned
+  for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const uint32_t v0 = (uint32_t)(t / tl) * kCompV, j0 = (uint32_t)(t % tl) * kCompL;
+    {
+      // thread: row tid / 8, lanes 4 * (tid % 8) .. + 3 of the tile
+      const uint32_t rr = tid >> 3, c0 = (tid & 7u) * 4u;
+      const uint32_t v = v0 + rr, j = j0 + c0;
+      int32_t e[4] = {-1, -1, -1, -1};
+      if (v < n) {
+        const int32_t *row = P + (uint64_t)v * R;
+        if (vec && j + 3 < R) {
+          const int4 x4 = __ldcg(reinterpret_cast<const int4 *>(row + j));
+          e[0] = x4.x; e[1] = x4.y; e[2] = x4.z; e[3] = x4.w;
+        } else {
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            if (j + q < R) e[q] = __ldcg(row + j + q);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) tile[rr][c0 + q] = e[q];
+    }
+    __syncthreads();
+    // warp w: tile lanes w, w + 8, w + 16, w + 24 of the 32 vertices; the
+    // first parent loads of the four items are issued together
+    const uint32_t v = v0 + lane;
+    int32_t x[4], r[4];
+    bool live[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      x[q] = tile[lane][warp + 8u * q];
+      r[q] = x[q];
+      live[q] = x[q] >= 0;  // out-of-range slots were loaded as -1
+    }
+    int32_t y[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      y[q] = live[q] ? __ldcg(P + (uint64_t)(uint32_t)r[q] * R + (j0 + warp + 8u * q)) : -1;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const uint32_t j = j0 + warp + 8u * q;
+      if (live[q] && y[q] >= 0) {  // parent is not the root: follow the chain
+        r[q] = y[q];
+        uint32_t it = 1;
+        for (; it < cap; ++it) {
+          const int32_t z = __ldcg(P + (uint64_t)(uint32_t)r[q] * R + j);
+          if (z < 0) break;
+          r[q] = z;
+        }
+        if (it == cap) {
+          set_status(status, IM_ETIMEOUT);
+          live[q] = false;
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const uint32_t j = j0 + warp + 8u * q;
+      const uint32_t key = live[q] ? (uint32_t)r[q] : 0xffffffffu;
+      const unsigned peers = __match_any_sync(kFull, key);
+      if (live[q]) {
+        if (lane == (uint32_t)(__ffs(peers) - 1))
+          atomicAdd(P + (uint64_t)(uint32_t)r[q] * R + j, -(int32_t)__popc(peers));
+        if (r[q] != x[q]) __stcg(P + (uint64_t)v * R + j, r[q]);
+      }
+    }
+    __syncthreads();  // the tile is reloaded next iteration
   }
 }
 
 cudaError_t launch_compress(const im_graph *g, const im_workspace *ws, const QueryParams &q,
                             cudaStream_t s) {
-  uint32_t nR = (uint32_t)((uint64_t)g->n * q.R);
-  uint64_t blocks = ((uint64_t)nR / 4 + 255) / 256;
-  uint64_t cap = (uint64_t)g->num_sms * 8;
+  const uint64_t ntiles = ((uint64_t)g->n + kCompV - 1) / kCompV * ((q.R + kCompL - 1) / kCompL);
+  uint64_t blocks = ntiles;
+  const uint64_t cap = (uint64_t)g->num_sms * 8;
   if (blocks > cap) blocks = cap;
   if (blocks == 0) blocks = 1;
-  k_compress<<<(unsigned)blocks, 256, 0, s>>>(ws->d_P, nR, q.R, ws->d_status,
+  k_compress<<<(unsigned)blocks, 256, 0, s>>>(ws->d_P, (uint32_t)g->n, q.R, ws->d_status,
                                               uf_cap((uint32_t)g->n));
   return cudaGetLastError();
 }
