@@ -353,6 +353,17 @@ def run_ours(args, xadj, adj, w):
             a = b / (prof[ph][0] / prof[ph][1] / 1e3) / 1e9
             hbm["k_" + ph] = {"achieved_gbs": a, "frac": a / peak, "bytes_per_launch": b}
 
+    # The component pipeline (label init, fused sample + union, size memo,
+    # first gains) against its algorithmic floor 8m + 20nR bytes per query:
+    # the CSR once, labels written, read for sizes, sizes written, labels and
+    # sizes read for the first gains.
+    cc_phases = ("prep", "union", "compress", "gains")
+    cc_us = sum(prof[ph][0] / prof[ph][1] * 1e3 for ph in cc_phases if prof[ph][1])
+    cc_bytes = 8 * m + 4 * (n + 1) + 20 * n * R
+    cc_gbs = cc_bytes / (cc_us / 1e6) / 1e9
+    cc = {"phases": list(cc_phases), "us_per_query": cc_us, "bytes_per_query": cc_bytes,
+          "achieved_gbs": cc_gbs, "frac": cc_gbs / peak, "peak": peak, "peak_kind": peak_kind}
+
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -360,6 +371,7 @@ def run_ours(args, xadj, adj, w):
         "config": workload_config(args.workload, xadj, adj, w),
         "select_plus_spread_ms_per_query": total_ms / args.steps / len(ps),
         "gpu_launches": int(launches), "roofline": roof, "hbm_kernels": hbm,
+        "component_pipeline": cc,
         "per_kernel": per_kernel, "per_p": by_p, "clocks": clock_info, "consistent_spread": consistent,
         "paper_context": "NetHEP (15,235 v / 58,892 e), K=50, p=0.01: 0.08 s on 2x Xeon "
                          "E5-2620v4, 16 threads (Table 4); R not stated",

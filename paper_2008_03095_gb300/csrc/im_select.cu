@@ -384,6 +384,18 @@ __global__ void __launch_bounds__(256) k_compress(int32_t *P, uint32_t n, uint32
         if (it == cap) {
           set_status(status, IM_ETIMEOUT);
           live[q] = false;
+        } else if (it > 1) {
+          // Full path compression: the chain's inner nodes (non-roots of the
+          // same component) get the root too, so later walks through them
+          // take one step. Their own slots are written with the same value
+          // when their tiles come round, so no update is lost.
+          int32_t z = x[q];  // the first parent; the walk stops at the root
+          for (uint32_t k = 0; k < it && z != r[q]; ++k) {
+            const int32_t nz = __ldcg(P + (uint64_t)(uint32_t)z * R + j);
+            if (nz < 0) break;
+            __stcg(P + (uint64_t)(uint32_t)z * R + j, r[q]);
+            z = nz;
+          }
         }
       }
     }
