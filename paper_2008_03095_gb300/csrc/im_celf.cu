@@ -1,7 +1,9 @@
 // On-device lazy greedy (CELF) seed selection over the memoized samples
-// (Algorithm 7 lines 3-18; CELF of Section 2.2): one cooperative launch with
-// one 1024-thread block per SM. Block 0 drives the lazy greedy; all blocks
-// join for the grid-wide steps (prefix extraction and bulk gain refresh).
+// (Algorithm 7; CELF of Section 2.2): one cooperative launch of 1024-thread
+// blocks (one per SM for graphs above 65536 vertices, a quarter of the SMs
+// below, where only the bulk refresh needs the grid). Block 0 drives the lazy
+// greedy; all blocks join for the grid-wide steps (prefix extraction and bulk
+// gain refresh).
 //
 // Keys pack (gain << 32) | (0xffffffff - v): a larger key means a larger gain
 // and, on equal gains, a smaller vertex id, so the key order is exactly the
@@ -955,7 +957,12 @@ cudaError_t launch_celf(const im_graph *g, const im_workspace *ws, const QueryPa
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kCelfThreads, dyn);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
-  dim3 grid(g->num_sms), block(kCelfThreads);
+  // With the single-block extraction the other blocks only join the bulk
+  // refresh, so a quarter of the SMs suffices and the rest stay free for
+  // queries running concurrently on other streams; the grid-wide extraction
+  // of larger graphs takes every SM.
+  const int nblocks = (uint32_t)g->n <= kLocalN ? (g->num_sms + 3) / 4 : g->num_sms;
+  dim3 grid(nblocks), block(kCelfThreads);
   void *args[] = {&a};
   return cudaLaunchCooperativeKernel(fn, grid, block, args, dyn, s);
 }

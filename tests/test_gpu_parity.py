@@ -279,3 +279,36 @@ def test_invalid_inputs_keep_handles_usable(g2000):
     seeds, sigma = im.im_select_seeds(g, 10, 256, 0.01, 7)
     oseeds, osigma = oracle.select_seeds(xadj, adj, 10, 256, 0.01, 7)
     assert np.array_equal(seeds, oseeds) and np.array_equal(sigma, osigma)
+
+
+def test_concurrent_queries_on_streams_match_serial():
+    """Independent queries on three streams with three workspaces overlap on
+    the device; each result equals the same query run alone."""
+    import torch
+
+    xadj, adj = synth.workload_graph("powerlaw_n2000")
+    g = _graph(xadj, adj)
+    R, K, seed = 256, 10, 7
+    ps = (0.005, 0.01, 0.05)
+    alone = [im.im_select_seeds(g, K, R, p, seed) for p in ps]
+    dev = torch.device("cuda", 0)
+    streams = [torch.cuda.Stream(device=dev) for _ in ps]
+    wss = [im.im_workspace_create(g, R) for _ in ps]
+    d_seeds = torch.zeros((len(ps), K), dtype=torch.int32, device=dev)
+    d_sigma = torch.zeros((len(ps), K), dtype=torch.int64, device=dev)
+    d_spread = torch.zeros(len(ps), dtype=torch.int64, device=dev)
+    for _ in range(2):
+        for i, p in enumerate(ps):
+            im.im_set_stream(streams[i])
+            im.im_select_seeds_async(g, wss[i], K, R, p, seed, d_seeds[i], d_sigma[i])
+            im.im_estimate_spread_async(g, wss[i], d_seeds[i], K, R, p, seed, d_spread[i:i + 1])
+        torch.cuda.synchronize()
+        for i, p in enumerate(ps):
+            im.im_set_stream(streams[i])
+            im.im_workspace_status(wss[i])
+            assert np.array_equal(d_seeds[i].cpu().numpy(), alone[i][0])
+            assert np.array_equal(d_sigma[i].cpu().numpy().astype(np.uint64), alone[i][1])
+            assert int(d_spread[i].item()) == int(alone[i][1][-1])
+    im.im_set_stream(None)
+    for w_ in wss:
+        w_.close()
