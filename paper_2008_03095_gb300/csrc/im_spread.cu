@@ -258,6 +258,9 @@ cudaError_t launch_spread(const im_graph *g, const im_workspace *ws, const Query
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   if (per_sm > 2) per_sm = 2;
+  // Small tables: one block per SM keeps the per-level grid barrier cheap and
+  // leaves room for queries running concurrently on other streams.
+  if ((uint64_t)g->n * a.W < (4u << 20)) per_sm = 1;
   dim3 grid(g->num_sms * per_sm), block(512);
   void *args[] = {&a};
   return cudaLaunchCooperativeKernel((const void *)k_spread, grid, block, args, 0, s);
