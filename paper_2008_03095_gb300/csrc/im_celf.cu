@@ -19,9 +19,9 @@
 //   pool       the first B entries of C, evaluated exactly against the current
 //              seed set: per lane, the component root and the not yet covered
 //              component size, kept in shared memory.
-// Round (driver): evaluate the pool (the segmented reduce of Algorithm 7 lines
-// 14-16). While the best pool gain beats every other bound (the head of the
-// rest of C and sig_out), commit it (lines 11-12) and subtract, from every
+// Round (driver): evaluate the pool (the segmented reduce of marginal gains over
+// the R samples in Algorithm 7). While the best pool gain beats every other
+// bound (the head of the rest of C and sig_out), commit it and subtract, from every
 // other pool member, the lanes it shares a component with -- pool gains stay
 // exact, so several seeds can be committed per round. The round's seeds mark
 // their components covered in the per-sample bitmap; surviving pool members
@@ -110,8 +110,6 @@ struct CelfSmem {
   uint64_t sel_t, sel_A, sel_B;
   uint32_t sel_above;
   int sel_done;
-  uint64_t best_key;
-  int best_w;
 };
 
 __device__ __forceinline__ uint64_t make_key(uint32_t gain, int32_t v) {
@@ -481,6 +479,18 @@ struct Driver {
 // Block 0: lazy-greedy rounds over the prefix in shared memory until the
 // query is done or a grid step is needed. Returns the next command. POOL_SMEM:
 // the per-lane pool arrays live in shared memory (else in global memory).
+// Invariant check: the first violation (code, two values) goes to the work
+// counters and the status becomes IM_EINTERNAL; the caller keeps every index
+// in range.
+__device__ __forceinline__ void celf_violation(const CelfArgs &a, uint32_t code, uint64_t v0,
+                                               uint64_t v1) {
+  if (atomicCAS(a.status, 0, IM_EINTERNAL) == 0 && a.stats) {
+    a.stats[13] = code;
+    a.stats[14] = v0;
+    a.stats[15] = v1;
+  }
+}
+
 // i / R for i < 2^21 by a multiply-high with M = ceil(2^32 / R) and one
 // correction step (M = 0 encodes R = 1).
 __device__ __forceinline__ uint32_t div_R(uint32_t i, uint32_t R, uint32_t M) {
@@ -511,7 +521,13 @@ __device__ __noinline__ int drive_rounds(const CelfArgs &a, CelfSmem &s, uint32_
     ++d.rounds;
     const uint32_t np = (d.nC - d.head) < B ? (d.nC - d.head) : B;
     if (tid < (int)np) {
-      s.pid[tid] = key_vertex(s.C[d.head + tid]);
+      const uint64_t kv = s.C[d.head + tid];
+      int32_t v = key_vertex(kv);
+      if (kv == 0 || v < 0 || (uint32_t)v >= a.n) {  // cannot happen: record, stay in range
+        celf_violation(a, 1000u + (uint32_t)tid, kv, ((uint64_t)d.head << 32) | d.nC);
+        v = 0;
+      }
+      s.pid[tid] = v;
       s.pactive[0][tid] = 1;
     }
     const uint64_t kc = d.head + np < d.nC ? s.C[d.head + np] : 0ull;
