@@ -51,9 +51,12 @@ constexpr int kCap = 4096;     // candidate prefix capacity
 constexpr int kTarget = 2048;  // prefix size aimed for per extraction
 constexpr int kBins = 2048;    // histogram bins of the threshold search
 constexpr int kPoolMax = 32;
+// Blocks of the first thread-block cluster (the driver and its helpers) that
+// evaluate each round's pool together when the pool lives in shared memory.
+constexpr int kEvalCluster = 4;
 constexpr size_t kPoolSmemBudget = 160 * 1024;
 
-enum : int { kCmdExtract = 1, kCmdRefresh = 2, kCmdDone = 3, kCmdFail = 4 };
+enum : int { kCmdExtract = 1, kCmdRefresh = 2, kCmdDone = 3, kCmdFail = 4, kCmdEval = 5 };
 
 // Grid-shared control block (global memory).
 struct CelfCtl {
@@ -107,6 +110,8 @@ struct CelfSmem {
   int32_t committed[kPoolMax];
   uint64_t Y[kPoolMax];
   uint32_t ny;
+  int ccmd;      // driver -> helpers: kCmdEval or the command drive_rounds returns
+  uint32_t cnp;  // driver -> helpers: pool size of the round
   uint64_t sel_t, sel_A, sel_B;
   uint32_t sel_above;
   int sel_done;
@@ -500,23 +505,103 @@ __device__ __forceinline__ uint32_t div_R(uint32_t i, uint32_t R, uint32_t M) {
   return c;
 }
 
+// Exact gains of the pool's (candidate, lane) items, rank-th of nranks equal
+// shares: g(u | S) = sum_r [component of u in r not covered] * |C_r(u)|. A
+// thread issues the label loads of four items together, then their dependent
+// size and covered-bit gathers together; root and uncovered size of every
+// item go to proot / pcont (the driver's shared memory, possibly remote).
+__device__ __forceinline__ void eval_items(const CelfArgs &a, const int32_t *pid, uint32_t np,
+                                           uint32_t *proot, uint32_t *pcont, uint32_t rank,
+                                           uint32_t nranks) {
+  const uint32_t R = a.R;
+  const uint32_t items = np * R;
+  const uint32_t stride = nranks * kCelfThreads;
+  for (uint32_t base = rank * kCelfThreads + threadIdx.x; base < items; base += 4 * stride) {
+    int32_t xv[4];
+    uint32_t uv[4], jv[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const uint32_t i = base + q * stride;
+      xv[q] = -1;
+      uv[q] = 0;
+      jv[q] = 0;
+      if (i < items) {
+        const uint32_t c = div_R(i, R, a.magic_R);
+        jv[q] = i - c * R;
+        uv[q] = (uint32_t)pid[c];
+        xv[q] = __ldg(a.P + (size_t)uv[q] * R + jv[q]);
+      }
+    }
+    uint32_t szv[4], cwv[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int32_t x = xv[q];
+      const uint32_t root = x < 0 ? uv[q] : (uint32_t)x;
+      const uint32_t bit = root * R + jv[q];
+      szv[q] = 0;
+      cwv[q] = 0;
+      if (base + q * stride < items) {
+        // a singleton {u} (x == -1) is covered only if u is a seed
+        szv[q] = x < 0 ? (uint32_t)(-x) : (uint32_t)(-__ldg(a.P + (size_t)x * R + jv[q]));
+        cwv[q] = (x != -1) ? (__ldcg(a.cov + (bit >> 5)) >> (bit & 31)) & 1u : 0u;
+      }
+      uv[q] = root;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const uint32_t i = base + q * stride;
+      if (i < items) {
+        proot[i] = uv[q];
+        pcont[i] = cwv[q] ? 0u : szv[q];
+      }
+    }
+  }
+}
+
+// Helper blocks of the first cluster: evaluate their share of every round's
+// pool into the driver's shared memory until the driver announces another
+// command, which is returned.
+__device__ __noinline__ int helper_rounds(const CelfArgs &a, CelfSmem &s, uint32_t *dyn) {
+  cg::cluster_group cl = cg::this_cluster();
+  const CelfSmem *ds = cl.map_shared_rank(&s, 0);
+  uint32_t *rroot = cl.map_shared_rank(dyn, 0);
+  uint32_t *rcont = rroot + (size_t)a.B * a.R;
+  for (;;) {  // bounded by the driver's round budget: every driver exit is announced
+    cl.sync();  // the driver has published ccmd (and the pool)
+    const int cmd = *(volatile const int *)&ds->ccmd;
+    if (cmd != kCmdEval) return cmd;
+    const uint32_t np = *(volatile const uint32_t *)&ds->cnp;
+    eval_items(a, ds->pid, np, rroot, rcont, cl.block_rank(), kEvalCluster);
+    cl.sync();  // the driver reads the results
+  }
+}
+
 template <bool POOL_SMEM>
 __device__ __noinline__ int drive_rounds(const CelfArgs &a, CelfSmem &s, uint32_t *proot, uint32_t *pcont,
                             Driver &d) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t R = a.R;
   const uint32_t B = (uint32_t)a.B;
+  cg::cluster_group cl = cg::this_cluster();
+  // every exit is announced to the helper blocks of the cluster (POOL_SMEM)
+  auto leave = [&](int cmd) -> int {
+    if (POOL_SMEM) {
+      if (tid == 0) s.ccmd = cmd;
+      cl.sync();
+    }
+    return cmd;
+  };
   long long t_mark = clock64();
   for (;;) {
-    if (d.nsel >= a.K) return kCmdDone;
+    if (d.nsel >= a.K) return leave(kCmdDone);
     if (d.rounds >= a.round_cap) {
       if (tid == 0) set_status(a.status, IM_ETIMEOUT);
-      return kCmdFail;
+      return leave(kCmdFail);
     }
-    if (d.head >= d.nC || s.C[d.head] < d.sig_out) return kCmdExtract;
+    if (d.head >= d.nC || s.C[d.head] < d.sig_out) return leave(kCmdExtract);
     if (d.evals_since_commit >= a.refresh_after) {
       d.evals_since_commit = 0;  // the refresh makes every key exact
-      return kCmdRefresh;
+      return leave(kCmdRefresh);
     }
     ++d.rounds;
     const uint32_t np = (d.nC - d.head) < B ? (d.nC - d.head) : B;
@@ -537,52 +622,21 @@ __device__ __noinline__ int drive_rounds(const CelfArgs &a, CelfSmem &s, uint32_
     __syncthreads();
 
     // ---------------------------------------------------------- exact gains
-    // g(u | S) = sum_r [component of u in r not covered] * |C_r(u)|. All
-    // (candidate, lane) items are spread over the block in one pass: a thread
-    // issues the label loads of four items together, then their dependent
-    // size and covered-bit gathers together.
-    const uint32_t items = np * R;
-    for (uint32_t base = tid; base < items; base += 4 * kCelfThreads) {
-      int32_t xv[4];
-      uint32_t uv[4], jv[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const uint32_t i = base + q * kCelfThreads;
-        xv[q] = -1;
-        uv[q] = 0;
-        jv[q] = 0;
-        if (i < items) {
-          const uint32_t c = div_R(i, R, a.magic_R);
-          jv[q] = i - c * R;
-          uv[q] = (uint32_t)s.pid[c];
-          xv[q] = __ldg(a.P + (size_t)uv[q] * R + jv[q]);
-        }
+    // With the pool in shared memory the first cluster's blocks share the
+    // evaluation: the pool is published with one cluster barrier and the
+    // results are complete after the next.
+    if (POOL_SMEM) {
+      if (tid == 0) {
+        s.cnp = np;
+        s.ccmd = kCmdEval;
       }
-      uint32_t szv[4], cwv[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int32_t x = xv[q];
-        const uint32_t root = x < 0 ? uv[q] : (uint32_t)x;
-        const uint32_t bit = root * R + jv[q];
-        szv[q] = 0;
-        cwv[q] = 0;
-        if (base + q * kCelfThreads < items) {
-          // a singleton {u} (x == -1) is covered only if u is a seed
-          szv[q] = x < 0 ? (uint32_t)(-x) : (uint32_t)(-__ldg(a.P + (size_t)x * R + jv[q]));
-          cwv[q] = (x != -1) ? (__ldcg(a.cov + (bit >> 5)) >> (bit & 31)) & 1u : 0u;
-        }
-        uv[q] = root;
-      }
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const uint32_t i = base + q * kCelfThreads;
-        if (i < items) {
-          proot[i] = uv[q];
-          pcont[i] = cwv[q] ? 0u : szv[q];
-        }
-      }
+      cl.sync();
+      eval_items(a, s.pid, np, proot, pcont, 0, kEvalCluster);
+      cl.sync();
+    } else {
+      eval_items(a, s.pid, np, proot, pcont, 0, 1);
+      __syncthreads();
     }
-    __syncthreads();
     for (uint32_t m = (uint32_t)warp; m < np; m += kCelfWarps) {
       const uint32_t *cc = pcont + (size_t)m * R;
       uint32_t g = 0;
@@ -714,7 +768,7 @@ __device__ __noinline__ int drive_rounds(const CelfArgs &a, CelfSmem &s, uint32_
     }
     if (d.nsel >= a.K) {
       __syncthreads();
-      return kCmdDone;
+      return leave(kCmdDone);
     }
 
     // ---------------------------------------------------------- merge survivors back
@@ -901,6 +955,10 @@ __global__ void __launch_bounds__(kCelfThreads, 1) k_celf(CelfArgs a) {
       if (!ok || d.nC > (uint32_t)kCap || d.nC == 0) {
         if (tid == 0) set_status(a.status, IM_EINTERNAL);
         cmd = kCmdFail;
+        if (POOL_SMEM) {  // the helpers wait for the driver's first announcement
+          if (tid == 0) s.ccmd = kCmdFail;
+          cg::this_cluster().sync();
+        }
       } else {
         d.head = 0;
         sort_desc(s, d.nC);
@@ -915,6 +973,8 @@ __global__ void __launch_bounds__(kCelfThreads, 1) k_celf(CelfArgs a) {
       }
       __syncthreads();
       if (tid == 0) ctl->cmd = cmd;
+    } else if (POOL_SMEM && blockIdx.x < (unsigned)kEvalCluster) {
+      helper_rounds(a, s, dyn);
     }
     grid.sync();
     cmd = __ldcg(&ctl->cmd);
@@ -977,10 +1037,36 @@ cudaError_t launch_celf(const im_graph *g, const im_workspace *ws, const QueryPa
   // refresh, so a quarter of the SMs suffices and the rest stay free for
   // queries running concurrently on other streams; the grid-wide extraction
   // of larger graphs takes every SM.
-  const int nblocks = (uint32_t)g->n <= kLocalN ? (g->num_sms + 3) / 4 : g->num_sms;
-  dim3 grid(nblocks), block(kCelfThreads);
+  int nblocks = (uint32_t)g->n <= kLocalN ? (g->num_sms + 3) / 4 : g->num_sms;
   void *args[] = {&a};
-  return cudaLaunchCooperativeKernel(fn, grid, block, args, dyn, s);
+  if (!a.pool_smem) {
+    dim3 grid(nblocks), block(kCelfThreads);
+    return cudaLaunchCooperativeKernel(fn, grid, block, args, dyn, s);
+  }
+  // Shared-memory pool: clusters of kEvalCluster blocks (the first cluster
+  // evaluates each round's pool together), as many as can be co-resident.
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[2];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  attr[1].id = cudaLaunchAttributeClusterDimension;
+  attr[1].val.clusterDim.x = kEvalCluster;
+  attr[1].val.clusterDim.y = 1;
+  attr[1].val.clusterDim.z = 1;
+  cfg.blockDim = dim3(kCelfThreads);
+  cfg.dynamicSmemBytes = dyn;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 2;
+  cfg.gridDim = dim3(kEvalCluster);
+  int max_clusters = 0;
+  e = cudaOccupancyMaxActiveClusters(&max_clusters, fn, &cfg);
+  if (e != cudaSuccess) return e;
+  if (max_clusters < 1) return cudaErrorInvalidConfiguration;
+  int nclusters = (nblocks + kEvalCluster - 1) / kEvalCluster;
+  if (nclusters > max_clusters) nclusters = max_clusters;
+  cfg.gridDim = dim3(nclusters * kEvalCluster);
+  return cudaLaunchKernelExC(&cfg, fn, args);
 }
 
 }  // namespace imgb
