@@ -53,7 +53,7 @@ constexpr int kBins = 2048;    // histogram bins of the threshold search
 constexpr int kPoolMax = 32;
 // Blocks of the first thread-block cluster (the driver and its helpers) that
 // evaluate each round's pool together when the pool lives in shared memory.
-constexpr int kEvalCluster = 4;
+constexpr int kEvalCluster = 8;
 constexpr size_t kPoolSmemBudget = 160 * 1024;
 
 enum : int { kCmdExtract = 1, kCmdRefresh = 2, kCmdDone = 3, kCmdFail = 4, kCmdEval = 5 };
