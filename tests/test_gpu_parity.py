@@ -312,3 +312,18 @@ def test_concurrent_queries_on_streams_match_serial():
     im.im_set_stream(None)
     for w_ in wss:
         w_.close()
+
+
+@pytest.mark.parametrize("R", [20480, 20481, 32768])
+def test_large_R_pool_in_global_memory_and_wide_spread_rows(R):
+    """R above 20480 moves the lazy greedy's pool to global memory (20480 is
+    the last R whose pool of one candidate fits the shared-memory budget), and
+    R above 2048 gives spread rows wider than the register copy."""
+    xadj, adj = synth.random_graph(300, 900, 6)
+    g = _graph(xadj, adj)
+    seeds, sigma = im.im_select_seeds(g, 5, R, 0.05, 7)
+    oseeds, osigma = oracle.select_seeds(xadj, adj, 5, R, 0.05, 7)
+    assert np.array_equal(seeds, oseeds) and np.array_equal(sigma, osigma)
+    assert im.im_estimate_spread(g, seeds, R, 0.05, 7) == int(osigma[-1])
+    S = np.array([3, 77, 150, 3], dtype=np.int32)
+    assert im.im_estimate_spread(g, S, R, 0.05, 7) == oracle.estimate_spread(xadj, adj, S, R, 0.05, 7)
