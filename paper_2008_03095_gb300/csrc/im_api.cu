@@ -463,6 +463,7 @@ int im_graph_create(int32_t n, int64_t m, const int32_t *xadj, const int32_t *ad
   g->m = m;
   cudaError_t e = cudaGetDevice(&g->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g->l2_bytes, cudaDevAttrL2CacheSize, g->device);
   if (e != cudaSuccess) {
     delete g;
     return cuda_fail(e, "device query");

@@ -136,6 +136,7 @@ struct im_graph {
   int64_t m = 0;          // undirected edges = arcs / 2
   int device = 0;
   int num_sms = 0;
+  int l2_bytes = 0;       // device L2 size
   int32_t *d_xadj = nullptr;
   int32_t *d_adj = nullptr;
   int32_t *d_eu = nullptr;  // upper-triangle edge list, eu[e] < ev[e]

@@ -30,6 +30,7 @@ struct SpreadArgs {
   int nb;
   uint32_t T32;
   int all_live;
+  int precheck;         // read V before each atomicOr (table larger than L2)
   const uint8_t *mask;  // explicit-mask test mode: mask[arc * R + j]
   const int32_t *seeds;
   int num_seeds;
@@ -198,6 +199,11 @@ __global__ void __launch_bounds__(512) k_spread(SpreadArgs a) {
         }
         if (!nbits) continue;
         const uint64_t o = (uint64_t)v * W + w;
+        // V only gains bits during the launch, so a word read from L2 that
+        // already holds every live bit proves the atomic would gain nothing.
+        // When V does not fit in L2, revisited hubs then cost a read instead
+        // of an atomic; an L2-resident V takes the atomic at once.
+        if (a.precheck && (__ldcg(a.V + o) & nbits) == nbits) continue;
         const uint32_t old = atomicOr(a.V + o, nbits);
         const uint32_t gained = nbits & ~old;
         if (!gained) continue;
@@ -233,6 +239,7 @@ cudaError_t launch_spread(const im_graph *g, const im_workspace *ws, const Query
   a.nb = d_mask ? 0 : q.nb;
   a.T32 = q.T32;
   a.all_live = q.all_live;
+  a.precheck = (uint64_t)g->n * a.W * 4u > (uint64_t)g->l2_bytes;
   a.mask = d_mask;
   a.seeds = d_seeds;
   a.num_seeds = num_seeds;
