@@ -317,7 +317,7 @@ cudaError_t launch_union(const im_graph *g, const im_workspace *ws, const QueryP
 // ------------------------------------------------------------------ compress
 // Size memo (Section 3.3): every non-root slot gets its root (the component
 // minimum) and each root slot accumulates -|component|. The label table is
-// processed in tiles of 32 vertices x 8 lanes: the block loads a tile with
+// processed in tiles of 32 vertices x 32 lanes: the block loads a tile with
 // sector-sized row reads, then warp w takes lane j0 + w of the 32 vertices,
 // so the parent lookups of a warp hit one lane (vertices that share a parent,
 // as in a giant component, coalesce into one request) and the root counters
