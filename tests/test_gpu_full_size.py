@@ -4,6 +4,9 @@ on one stream).
 
 - powerlaw_n37154 (n = 37,154, R = 2048): the whole seed sequence and sigma*R
   equal the oracle's; labels and sizes of sampled simulations too.
+- powerlaw_n1250000 (R = 1024): the spread's visited table is larger than L2,
+  so the spread kernel reads each visited word before its atomic; the spread of
+  every prefix of the selected seeds equals sigma*R of that prefix.
 - clustered_n334863 and powerlaw_n4m (label tables of 2.7 and 8.2 GB): labels
   and sizes of sampled simulations equal the oracle's bit for bit, and the
   selection satisfies properties that hold at any size, checked with the spread
@@ -118,4 +121,21 @@ def test_powerlaw_n4m_sampled_parity_and_greedy_properties():
     _sampled_lanes_match(g, xadj, adj, w, p, [0, 511])
     seeds, sigma, spread = _select_like_bench(g, w, p)
     _greedy_properties(g, xadj, w, p, seeds, sigma, spread, np.random.default_rng(41))
+    g.close()
+
+
+def test_spread_with_visited_table_beyond_l2():
+    import torch
+
+    n, m, R, K, p, seed = 1_250_000, 5_000_000, 1024, 8, 0.01, 7
+    l2 = torch.cuda.get_device_properties(0).L2_cache_size
+    assert n * (R // 32) * 4 > l2  # the pre-read branch of the spread kernel
+    xadj, adj = synth.chung_lu(n, m, 2.2, 43)
+    g = im.im_graph_create(xadj, adj)
+    _sampled_lanes_match(g, xadj, adj, dict(R=R, rng_seed=seed), p, [0, 1023])
+    seeds, sigma = im.im_select_seeds(g, K, R, p, seed)
+    for k in range(K):
+        assert im.im_estimate_spread(g, seeds[:k + 1], R, p, seed) == int(sigma[k])
+    dup = np.concatenate([seeds[:3], seeds[:3]])
+    assert im.im_estimate_spread(g, dup, R, p, seed) == int(sigma[2])
     g.close()
