@@ -31,6 +31,7 @@ struct SpreadArgs {
   uint32_t T32;
   int all_live;
   int precheck;         // read V before each atomicOr (table larger than L2)
+  int xs_smem;          // the R lane randoms are staged in shared memory
   const uint8_t *mask;  // explicit-mask test mode: mask[arc * R + j]
   const int32_t *seeds;
   int num_seeds;
@@ -72,7 +73,31 @@ __device__ __forceinline__ void push_frontier(const SpreadArgs &a, int32_t v, ui
   }
 }
 
+// Live lanes among the frontier lanes f of word w (Eq. 2), two lanes per
+// step so that their loads of X overlap; xs is the shared-memory copy of the
+// lane randoms or the global one.
+__device__ __forceinline__ uint32_t live_lanes(uint32_t f, uint32_t w, const uint32_t *xs,
+                                               uint32_t h, uint32_t T32, int all_live) {
+  uint32_t nbits = 0;
+  while (f) {
+    const int b0 = __ffs(f) - 1;
+    f &= f - 1;
+    const int b1 = f ? __ffs(f) - 1 : b0;  // a lone last lane is tested twice
+    f &= f - 1;
+    const uint32_t x0 = xs[(w << 5) + (uint32_t)b0];
+    const uint32_t x1 = xs[(w << 5) + (uint32_t)b1];
+    nbits |= (uint32_t)lane_live(x0, h, T32, all_live) << b0;
+    nbits |= (uint32_t)lane_live(x1, h, T32, all_live) << b1;
+  }
+  return nbits;
+}
+
+// Up to this many lane randoms (32 KB) are staged in shared memory; the
+// frontier-bit tests then read them there instead of through L1.
+constexpr uint32_t kSpreadSmemLanes = 8192;
+
 __global__ void __launch_bounds__(512) k_spread(SpreadArgs a) {
+  extern __shared__ uint32_t sXs[];
   cg::grid_group grid = cg::this_grid();
   const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const uint64_t nthr = (uint64_t)gridDim.x * blockDim.x;
@@ -93,6 +118,8 @@ __global__ void __launch_bounds__(512) k_spread(SpreadArgs a) {
     a.chklev[i] = 0u;
   }
   if (tid == 0) *a.acc = 0ull;
+  if (a.xs_smem)
+    for (uint32_t j = threadIdx.x; j < a.R; j += blockDim.x) sXs[j] = a.Xs[j];
   grid.sync();
 
   // sources: deduplicated seed set (list 0, stamp 1), all R lanes reached
@@ -188,14 +215,16 @@ __global__ void __launch_bounds__(512) k_spread(SpreadArgs a) {
         if (k >= nw) continue;
         f &= lane_range_mask(w, j0, j1);
         uint32_t nbits = 0;
-        while (f) {  // test only the frontier lanes of this word
-          const int bit = __ffs(f) - 1;
-          f &= f - 1;
-          const uint32_t j = (w << 5) + (uint32_t)bit;
-          bool l;
-          if (a.mask) l = a.mask[(uint64_t)e * a.R + j] != 0;
-          else l = lane_live(__ldg(a.Xs + j), h, a.T32, a.all_live);
-          nbits |= (uint32_t)l << bit;
+        if (a.mask) {
+          while (f) {  // test only the frontier lanes of this word
+            const int bit = __ffs(f) - 1;
+            f &= f - 1;
+            nbits |= (uint32_t)(a.mask[(uint64_t)e * a.R + (w << 5) + (uint32_t)bit] != 0) << bit;
+          }
+        } else if (a.xs_smem) {
+          nbits = live_lanes(f, w, sXs, h, a.T32, a.all_live);
+        } else {
+          nbits = live_lanes(f, w, a.Xs, h, a.T32, a.all_live);
         }
         if (!nbits) continue;
         const uint64_t o = (uint64_t)v * W + w;
@@ -260,8 +289,10 @@ cudaError_t launch_spread(const im_graph *g, const im_workspace *ws, const Query
   a.out = d_sigma;
   a.status = ws->d_status;
   a.stats = ws->d_stats;
+  a.xs_smem = (!d_mask && q.R <= kSpreadSmemLanes) ? 1 : 0;
+  const size_t smem = a.xs_smem ? (size_t)q.R * sizeof(uint32_t) : 0;
   int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spread, 512, 0);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spread, 512, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   if (per_sm > 2) per_sm = 2;
@@ -270,7 +301,7 @@ cudaError_t launch_spread(const im_graph *g, const im_workspace *ws, const Query
   if ((uint64_t)g->n * a.W < (4u << 20)) per_sm = 1;
   dim3 grid(g->num_sms * per_sm), block(512);
   void *args[] = {&a};
-  return cudaLaunchCooperativeKernel((const void *)k_spread, grid, block, args, 0, s);
+  return cudaLaunchCooperativeKernel((const void *)k_spread, grid, block, args, smem, s);
 }
 
 }  // namespace imgb
