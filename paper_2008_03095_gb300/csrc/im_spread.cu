@@ -193,6 +193,7 @@ __global__ void __launch_bounds__(512) k_spread(SpreadArgs a) {
           }
         }
       }
+      bool tried = false, push = false;
       const uint32_t w0 = j0 >> 5;
       const uint32_t nw = j1 > j0 ? ((j1 - 1) >> 5) - w0 + 1 : 0u;
       uint32_t maxw = nw;
@@ -238,7 +239,39 @@ __global__ void __launch_bounds__(512) k_spread(SpreadArgs a) {
         if (!gained) continue;
         atomicOr(Fn + o, gained);
         local += __popc(gained);
-        if (atomicMax(a.stamp + v, next_stamp) < next_stamp) push_frontier(a, v, level + 1, Ln, Qn);
+        // One stamp attempt per chunk: after it, v is in the next list
+        // whether this thread or another one put it there.
+        if (!tried) {
+          tried = true;
+          push = atomicMax(a.stamp + v, next_stamp) < next_stamp;
+        }
+      }
+      // The warp appends its new frontier vertices together: one atomic on
+      // each level counter per warp, chunk slots from a warp prefix sum.
+      const unsigned pm = __ballot_sync(kFull, push);
+      if (pm) {
+        uint32_t nch = 0;
+        if (push) nch = ((uint32_t)(a.xadj[v + 1] - a.xadj[v]) + 31u) >> 5;
+        uint32_t incl = nch;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+          const uint32_t t = __shfl_up_sync(kFull, incl, d);
+          if (lane >= d) incl += t;
+        }
+        const uint32_t total = __shfl_sync(kFull, incl, 31);
+        const int leader = __ffs(pm) - 1;
+        uint32_t lbase = 0, qbase = 0;
+        if (lane == leader) {
+          lbase = atomicAdd(a.cntlev + level + 1, (uint32_t)__popc(pm));
+          if (total) qbase = atomicAdd(a.chklev + level + 1, total);
+        }
+        lbase = __shfl_sync(kFull, lbase, leader);
+        qbase = __shfl_sync(kFull, qbase, leader);
+        if (push) {
+          Ln[lbase + (uint32_t)__popc(pm & ((1u << lane) - 1u))] = v;
+          const uint32_t q0 = qbase + incl - nch;
+          for (uint32_t c = 0; c < nch; ++c) Qn[q0 + c] = ((uint64_t)(uint32_t)v << 32) | c;
+        }
       }
     }
     grid.sync();
