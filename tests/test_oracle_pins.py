@@ -357,3 +357,30 @@ def test_oracle_rejects_invalid_csr():
         oracle.select_seeds(xadj, adj, 51, 8, 0.1, 1)  # K > n
     with pytest.raises(ValueError):
         oracle.select_seeds(xadj, adj, 3, 8, 1.5, 1)  # p > 1
+
+
+@pytest.mark.parametrize("p", [0.02, 0.2])
+def test_lane_sharding_invariance_of_gains_and_greedy(p):
+    # Samples are independent, so lane ranges [0, R1) and [R1, R) can be
+    # processed apart: their tables equal the matching columns of the full
+    # tables, marginal gains are sums over the shards, and a greedy that sums
+    # the shards' gains before each deterministic commit (gain desc, id asc)
+    # picks the same seeds and sigma*R as the single-range greedy.
+    xadj, adj = synth.chung_lu(150, 500, 2.3, 17)
+    n, R, seed, K = 150, 37, 9, 8
+    full_lab, full_siz = oracle.labels(xadj, adj, R, p, seed)
+    shards = [np.arange(0, 13), np.arange(13, R)]
+    tabs = [oracle.labels_lanes(xadj, adj, R, p, seed, lanes) for lanes in shards]
+    for lanes, (lab, siz) in zip(shards, tabs):
+        assert np.array_equal(lab, full_lab[:, lanes])
+        assert np.array_equal(siz, full_siz[:, lanes])
+    seeds, sigma = oracle.select_seeds(xadj, adj, K, R, p, seed)
+    S, total = [], 0
+    for k in range(K):
+        g = sum(oracle.marginal_gains(lab, siz, S).astype(np.int64) for lab, siz in tabs)
+        assert np.array_equal(g, oracle.marginal_gains(full_lab, full_siz, S).astype(np.int64))
+        g[S] = -1
+        best = int(np.argmax(g))
+        total += int(g[best])
+        assert seeds[k] == best and int(sigma[k]) == total
+        S.append(best)
