@@ -46,6 +46,19 @@ namespace cg = cooperative_groups;
 namespace imgb {
 
 constexpr int kCelfThreads = 1024;
+
+// Zero the contributions of the lanes whose root equals the committed seed's
+// root (the lanes the seed now covers), adding them to dsum; true when any
+// of the four lanes changed.
+__device__ __forceinline__ bool drop_shared4(uint4 &cv, const uint4 r, const uint4 b,
+                                             uint32_t &dsum) {
+  bool dirty = false;
+  if (cv.x && r.x == b.x) { dsum += cv.x; cv.x = 0; dirty = true; }
+  if (cv.y && r.y == b.y) { dsum += cv.y; cv.y = 0; dirty = true; }
+  if (cv.z && r.z == b.z) { dsum += cv.z; cv.z = 0; dirty = true; }
+  if (cv.w && r.w == b.w) { dsum += cv.w; cv.w = 0; dirty = true; }
+  return dirty;
+}
 constexpr int kCelfWarps = kCelfThreads / 32;
 constexpr int kCap = 4096;     // candidate prefix capacity
 constexpr int kTarget = 2048;  // prefix size aimed for per extraction
@@ -699,16 +712,22 @@ __device__ __noinline__ int drive_rounds(const CelfArgs &a, CelfSmem &s, uint32_
             const uint4 *rb4 = reinterpret_cast<const uint4 *>(rb);
             const uint4 *rr4 = reinterpret_cast<const uint4 *>(rr);
             uint4 *cc4 = reinterpret_cast<uint4 *>(cc);
-            for (uint32_t q = lane; q < (R >> 2); q += 32) {
-              uint4 cv = cc4[q];
-              if (!(cv.x | cv.y | cv.z | cv.w)) continue;
-              const uint4 r = rr4[q], b = rb4[q];
-              bool dirty = false;
-              if (cv.x && r.x == b.x) { dsum += cv.x; cv.x = 0; dirty = true; }
-              if (cv.y && r.y == b.y) { dsum += cv.y; cv.y = 0; dirty = true; }
-              if (cv.z && r.z == b.z) { dsum += cv.z; cv.z = 0; dirty = true; }
-              if (cv.w && r.w == b.w) { dsum += cv.w; cv.w = 0; dirty = true; }
-              if (dirty) cc4[q] = cv;
+            // Two 16-byte groups per lane and step, all six loads issued
+            // before any store, so a step costs one L2 round trip.
+            const uint32_t R4 = R >> 2;
+            for (uint32_t q = lane; q < R4; q += 64) {
+              const uint32_t q1 = q + 32;
+              const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+              uint4 cv0 = cc4[q];
+              const uint4 r0 = rr4[q], b0 = rb4[q];
+              uint4 cv1 = z, r1 = z, b1 = z;
+              if (q1 < R4) {
+                cv1 = cc4[q1];
+                r1 = rr4[q1];
+                b1 = rb4[q1];
+              }
+              if (drop_shared4(cv0, r0, b0, dsum)) cc4[q] = cv0;
+              if (drop_shared4(cv1, r1, b1, dsum)) cc4[q1] = cv1;
             }
           } else {
             for (uint32_t j = lane; j < R; j += 32) {
