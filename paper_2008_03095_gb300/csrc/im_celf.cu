@@ -713,7 +713,8 @@ __device__ __noinline__ int drive_rounds(const CelfArgs &a, CelfSmem &s, uint32_
             const uint4 *rr4 = reinterpret_cast<const uint4 *>(rr);
             uint4 *cc4 = reinterpret_cast<uint4 *>(cc);
             // Two 16-byte groups per lane and step, all six loads issued
-            // before any store, so a step costs one L2 round trip.
+            // before any store, so a step waits for one memory round trip
+            // (shared memory when the pool fits there, else global).
             const uint32_t R4 = R >> 2;
             for (uint32_t q = lane; q < R4; q += 64) {
               const uint32_t q1 = q + 32;
