@@ -327,3 +327,30 @@ def test_large_R_pool_in_global_memory_and_wide_spread_rows(R):
     assert im.im_estimate_spread(g, seeds, R, 0.05, 7) == int(osigma[-1])
     S = np.array([3, 77, 150, 3], dtype=np.int32)
     assert im.im_estimate_spread(g, S, R, 0.05, 7) == oracle.estimate_spread(xadj, adj, S, R, 0.05, 7)
+
+
+@pytest.mark.parametrize("p", [0.02, 0.2])
+def test_lane_ranges_on_gpu_sum_to_the_full_selection(p):
+    """Two lane ranges computed one after the other on the GPU give the
+    matching columns of the full tables, and summing the two ranges' marginal
+    gains on the host before each commit (gain desc, id asc) reproduces the
+    seeds and sigma*R that the GPU selects over the full range."""
+    xadj, adj = synth.chung_lu(400, 1600, 2.3, 23)
+    R, seed, K = 96, 7, 8
+    g = _graph(xadj, adj)
+    full_lab = im.im_debug_labels(g, R, p, seed)
+    full_siz = im.im_debug_sizes(g, R, p, seed)
+    shards = [np.arange(0, 40), np.arange(40, R)]
+    tabs = [im.im_debug_tables_lanes(g, R, p, seed, lanes) for lanes in shards]
+    for lanes, (lab, siz) in zip(shards, tabs):
+        assert np.array_equal(lab, full_lab[:, lanes])
+        assert np.array_equal(siz, full_siz[:, lanes])
+    seeds, sigma = im.im_select_seeds(g, K, R, p, seed)
+    S, total = [], 0
+    for k in range(K):
+        gsum = sum(oracle.marginal_gains(lab, siz, S).astype(np.int64) for lab, siz in tabs)
+        gsum[S] = -1
+        best = int(np.argmax(gsum))
+        total += int(gsum[best])
+        assert seeds[k] == best and int(sigma[k]) == total
+        S.append(best)
