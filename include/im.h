@@ -230,6 +230,12 @@ int im_debug_tables_lanes(const im_graph *g, int32_t R, double p, uint32_t rng_s
                           const int32_t *lanes, int32_t num_lanes, int32_t *out_labels,
                           uint32_t *out_sizes);
 
+/* First-seed marginal gains of the NewGreedy step (Algorithm 5, final loop):
+ * out_mg[v] = sum_r |C_r(v)|, the n values the lazy greedy starts from, as
+ * the device computed them (host array of n uint64 values). */
+int im_debug_first_gains(const im_graph *g, int32_t R, double p, uint32_t rng_seed,
+                         uint64_t *out_mg);
+
 /* Size memo (Section 3.3): out[l*R + r] = #{v : label of v in sample r is l},
  * zero where l is not a component label of sample r. */
 int im_debug_sizes(const im_graph *g, int32_t R, double p, uint32_t rng_seed,
@@ -252,6 +258,22 @@ int im_debug_select_seeds_masked(const im_graph *g, int32_t K, int32_t R, const 
 /* Spread with an explicit live mask (same layout as above). */
 int im_debug_estimate_spread_masked(const im_graph *g, const int32_t *seeds, int32_t num_seeds,
                                     int32_t R, const uint8_t *mask, uint64_t *out_sigma_R);
+
+/* Test-only, process-wide overrides of launch shapes, loop budgets and
+ * allocation outcomes, so that tests can drive the paths a healthy run never
+ * takes. value 0 restores the library's own choice. Keys: */
+enum {
+  IM_OVR_CELF_CLUSTER = 0,     /* lazy-greedy launch: -1 = plain cooperative launch without a
+                                  cluster attribute; c in {1, 2, 4, 8} = clusters of c blocks */
+  IM_OVR_CELF_ROUND_CAP = 1,   /* budget of lazy-greedy rounds (exceeded: IM_ETIMEOUT) */
+  IM_OVR_UF_CAP = 2,           /* budget of each union-find walk (exceeded: IM_ETIMEOUT) */
+  IM_OVR_SPREAD_LEVEL_CAP = 3, /* budget of spread BFS levels (exceeded: IM_ETIMEOUT) */
+  IM_OVR_FAIL_ALLOC = 4,       /* the value-th device allocation from now fails as if the
+                                  device were out of memory (1 = the next one); one shot */
+  IM_NUM_OVERRIDES = 5
+};
+/* Errors: IM_EINVAL (unknown key, or a value outside the key's range). */
+int im_debug_override(int32_t key, int64_t value);
 
 #ifdef __cplusplus
 }

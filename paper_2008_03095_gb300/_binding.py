@@ -73,6 +73,8 @@ def lib():
         "im_debug_edge_hash": [P, P, i64, P],
         "im_debug_select_seeds_masked": [P, i32, i32, P, P, P, P, P],
         "im_debug_estimate_spread_masked": [P, P, i32, i32, P, P],
+        "im_debug_override": [i32, i64],
+        "im_debug_first_gains": [P, i32, f64, u32, P],
         "im_profile_enable": [ctypes.c_int],
         "im_profile_read": [P, P],
     }
@@ -313,6 +315,13 @@ def im_debug_tables_lanes(g, R, p, rng_seed, lanes):
     return lab, siz
 
 
+def im_debug_first_gains(g, R, p, rng_seed):
+    """uint64[n]: mg_v = sum_r |C_r(v)| as computed on the device."""
+    out = np.empty(g.n, dtype=np.uint64)
+    _check(lib().im_debug_first_gains(_gh(g), R, p, rng_seed & 0xFFFFFFFF, _ptr(out)))
+    return out
+
+
 def im_debug_sizes(g, R, p, rng_seed):
     out = np.empty((g.n, R), dtype=np.uint32)
     _check(lib().im_debug_sizes(_gh(g), R, p, rng_seed & 0xFFFFFFFF, _ptr(out)))
@@ -343,6 +352,24 @@ def im_debug_select_seeds_masked(g, K, mask, tables=False):
     _check(lib().im_debug_select_seeds_masked(_gh(g), K, R, _ptr(mask), _ptr(seeds), _ptr(sigma),
                                               _ptr(lab), _ptr(siz)))
     return (seeds, sigma, lab, siz) if tables else (seeds, sigma)
+
+
+IM_OVR_CELF_CLUSTER = 0
+IM_OVR_CELF_ROUND_CAP = 1
+IM_OVR_UF_CAP = 2
+IM_OVR_SPREAD_LEVEL_CAP = 3
+IM_OVR_FAIL_ALLOC = 4
+IM_NUM_OVERRIDES = 5
+
+
+def im_debug_override(key, value):
+    """Test-only process-wide override (IM_OVR_* key; value 0 restores the default)."""
+    _check(lib().im_debug_override(key, value))
+
+
+def im_debug_clear_overrides():
+    for k in range(IM_NUM_OVERRIDES):
+        lib().im_debug_override(k, 0)
 
 
 def im_debug_estimate_spread_masked(g, seeds, mask):

@@ -56,6 +56,40 @@ static_assert(NoallocLayout::kR <= (size_t)kSortSmemMax, "lane sort must stay in
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NoallocLayout::bytes];
 
+// ------------------------------------------------------------------ test overrides
+namespace {
+std::atomic<int64_t> g_override[IM_NUM_OVERRIDES];
+}  // namespace
+
+namespace imgb {
+
+int64_t override_value(int key) {
+  return (key >= 0 && key < IM_NUM_OVERRIDES) ? g_override[key].load() : 0;
+}
+
+cudaError_t dev_malloc(void **p, size_t bytes) {
+  // IM_OVR_FAIL_ALLOC counts down to the allocation that is made to fail
+  int64_t k = g_override[IM_OVR_FAIL_ALLOC].load();
+  while (k > 0) {
+    if (g_override[IM_OVR_FAIL_ALLOC].compare_exchange_weak(k, k - 1)) {
+      if (k == 1) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+      }
+      break;
+    }
+  }
+  return cudaMalloc(p, bytes);
+}
+
+uint32_t uf_budget(uint32_t n) {
+  const uint32_t cap = uf_cap(n);
+  const int64_t o = override_value(IM_OVR_UF_CAP);
+  return (o > 0 && (uint64_t)o < cap) ? (uint32_t)o : cap;
+}
+
+}  // namespace imgb
+
 namespace {
 
 thread_local std::string t_err;
@@ -165,7 +199,7 @@ int make_params(const im_graph *g, int32_t R, double p, uint32_t seed, QueryPara
 
 template <class T>
 cudaError_t dalloc(T **p, size_t count) {
-  return cudaMalloc(reinterpret_cast<void **>(p), sizeof(T) * (count ? count : 1));
+  return dev_malloc(reinterpret_cast<void **>(p), sizeof(T) * (count ? count : 1));
 }
 
 void ws_free(im_workspace *ws) {
@@ -199,7 +233,7 @@ int ws_create(const im_graph *g, int32_t R_max, im_workspace **out) {
   WS_ALLOC(d_keys, n);
   WS_ALLOC(d_keyrange, 2);
   WS_ALLOC(d_chosen, n);
-  if (e == cudaSuccess) e = cudaMalloc(&ws->d_celf_ctl, celf_ctl_bytes());
+  if (e == cudaSuccess) e = dev_malloc(&ws->d_celf_ctl, celf_ctl_bytes());
   WS_ALLOC(d_pool, (size_t)R_max * 8 > (size_t)160 * 1024 ? (size_t)2 * 8 * R_max : 1);
   WS_ALLOC(d_X, R_max);
   WS_ALLOC(d_Xs, R_max);
@@ -318,7 +352,8 @@ int ensure_mask(im_workspace *ws, size_t bytes) {
   if (ws->d_mask) cudaFree(ws->d_mask);
   ws->d_mask = nullptr;
   ws->mask_cap = 0;
-  API_CUDA(cudaMalloc(&ws->d_mask, bytes ? bytes : 1), "cudaMalloc mask");
+  API_CUDA(dev_malloc(reinterpret_cast<void **>(&ws->d_mask), bytes ? bytes : 1),
+           "cudaMalloc mask");
   ws->mask_cap = bytes;
   return IM_OK;
 }
@@ -438,6 +473,17 @@ int im_profile_read(double *total_ms, int64_t *launches) {
 }
 
 uint64_t im_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+int im_debug_override(int32_t key, int64_t value) {
+  if (key < 0 || key >= IM_NUM_OVERRIDES) return fail(IM_EINVAL, "unknown override key %d", key);
+  if (key == IM_OVR_CELF_CLUSTER && !(value == 0 || value == -1 || value == 1 || value == 2 ||
+                                      value == 4 || value == 8))
+    return fail(IM_EINVAL, "cluster override %lld not in {0, -1, 1, 2, 4, 8}", (long long)value);
+  if (key != IM_OVR_CELF_CLUSTER && value < 0)
+    return fail(IM_EINVAL, "override %d must be >= 0", key);
+  g_override[key].store(value);
+  return IM_OK;
+}
 
 int im_sampling_threshold(double p, uint64_t *out_T) {
   if (!out_T) return fail(IM_EINVAL, "null output");
@@ -762,6 +808,31 @@ int im_debug_tables_lanes(const im_graph *g_, int32_t R, double p, uint32_t rng_
   if (d_siz) cudaFree(d_siz);
   if (e != cudaSuccess) return cuda_fail(e, "debug tables on selected simulations");
   return take_status(ws, s);
+}
+
+int im_debug_first_gains(const im_graph *g_, int32_t R, double p, uint32_t rng_seed,
+                         uint64_t *out_mg) {
+  if (!g_ || !out_mg) return fail(IM_EINVAL, "null argument");
+  im_graph *g = const_cast<im_graph *>(g_);
+  QueryParams q;
+  int rc = make_params(g, R, p, rng_seed, &q);
+  if (rc != IM_OK) return rc;
+  std::lock_guard<std::mutex> lock(g->mu);
+  DeviceGuard dg(g->device);
+  im_workspace *ws = nullptr;
+  rc = internal_ws(g, R, &ws);
+  if (rc != IM_OK) return rc;
+  cudaStream_t s = t_stream;
+  rc = enqueue_select(g, ws, 0, q, nullptr, nullptr, nullptr, s, true);
+  if (rc != IM_OK) return rc;
+  API_CUDA(launch_gains(g, ws, q, s), "k_gains");
+  std::vector<uint64_t> keys((size_t)g->n);
+  API_CUDA(cudaMemcpyAsync(keys.data(), ws->d_keys, sizeof(uint64_t) * g->n,
+                           cudaMemcpyDeviceToHost, s), "copy keys");
+  rc = take_status(ws, s);
+  if (rc != IM_OK) return rc;
+  for (int32_t v = 0; v < g->n; ++v) out_mg[v] = keys[(size_t)v] >> 32;  // key = mg << 32 | ~v
+  return IM_OK;
 }
 
 int im_debug_sizes(const im_graph *g, int32_t R, double p, uint32_t rng_seed,

@@ -549,14 +549,23 @@ __device__ __forceinline__ void eval_items(const CelfArgs &a, const int32_t *pid
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int32_t x = xv[q];
-      const uint32_t root = x < 0 ? uv[q] : (uint32_t)x;
-      const uint32_t bit = root * R + jv[q];
+      uint32_t root = x < 0 ? uv[q] : (uint32_t)x;
       szv[q] = 0;
       cwv[q] = 0;
       if (base + q * stride < items) {
-        // a singleton {u} (x == -1) is covered only if u is a seed
-        szv[q] = x < 0 ? (uint32_t)(-x) : (uint32_t)(-__ldg(a.P + (size_t)x * R + jv[q]));
-        cwv[q] = (x != -1) ? (__ldcg(a.cov + (bit >> 5)) >> (bit & 31)) & 1u : 0u;
+        if (root >= a.n) {  // a label outside [0, n) cannot come from the size pass
+          celf_violation(a, 2000u, root, ((uint64_t)uv[q] << 32) | jv[q]);
+          root = uv[q];
+        } else {
+          const uint32_t bit = root * R + jv[q];
+          // a singleton {u} (x == -1) is covered only if u is a seed
+          szv[q] = x < 0 ? (uint32_t)(-x) : (uint32_t)(-__ldg(a.P + (size_t)x * R + jv[q]));
+          cwv[q] = (x != -1) ? (__ldcg(a.cov + (bit >> 5)) >> (bit & 31)) & 1u : 0u;
+          if (szv[q] > a.n) {
+            celf_violation(a, 2001u, szv[q], ((uint64_t)uv[q] << 32) | jv[q]);
+            szv[q] = 0;
+          }
+        }
       }
       uv[q] = root;
     }
@@ -571,20 +580,23 @@ __device__ __forceinline__ void eval_items(const CelfArgs &a, const int32_t *pid
   }
 }
 
-// Helper blocks of the first cluster: evaluate their share of every round's
-// pool into the driver's shared memory until the driver announces another
-// command, which is returned.
+// Helper blocks of the driver's cluster: evaluate their share of every
+// round's pool into the driver's shared memory until the driver announces
+// another command, which is returned. The shares are cut by the cluster's
+// actual size and rank, read at run time, so that every (candidate, lane)
+// item is written whatever cluster shape the launch received.
 __device__ __noinline__ int helper_rounds(const CelfArgs &a, CelfSmem &s, uint32_t *dyn) {
   cg::cluster_group cl = cg::this_cluster();
   const CelfSmem *ds = cl.map_shared_rank(&s, 0);
   uint32_t *rroot = cl.map_shared_rank(dyn, 0);
   uint32_t *rcont = rroot + (size_t)a.B * a.R;
+  const uint32_t rank = cl.block_rank(), nranks = cl.num_blocks();
   for (;;) {  // bounded by the driver's round budget: every driver exit is announced
     cl.sync();  // the driver has published ccmd (and the pool)
     const int cmd = *(volatile const int *)&ds->ccmd;
     if (cmd != kCmdEval) return cmd;
     const uint32_t np = *(volatile const uint32_t *)&ds->cnp;
-    eval_items(a, ds->pid, np, rroot, rcont, cl.block_rank(), kEvalCluster);
+    eval_items(a, ds->pid, np, rroot, rcont, rank, nranks);
     cl.sync();  // the driver reads the results
   }
 }
@@ -644,7 +656,7 @@ __device__ __noinline__ int drive_rounds(const CelfArgs &a, CelfSmem &s, uint32_
         s.ccmd = kCmdEval;
       }
       cl.sync();
-      eval_items(a, s.pid, np, proot, pcont, 0, kEvalCluster);
+      eval_items(a, s.pid, np, proot, pcont, 0, cl.num_blocks());
       cl.sync();
     } else {
       eval_items(a, s.pid, np, proot, pcont, 0, 1);
@@ -766,8 +778,13 @@ __device__ __noinline__ int drive_rounds(const CelfArgs &a, CelfSmem &s, uint32_
         const uint32_t ci = t / groups;
         const uint32_t c = (uint32_t)s.committed[ci];
         const uint32_t j = (t - ci * groups) * 32 + (uint32_t)lane;
-        const uint32_t cv = pcont[(size_t)c * R + j];
-        const uint32_t word = cv ? (proot[(size_t)c * R + j] * R + j) >> 5 : 0xffffffffu;
+        uint32_t cv = pcont[(size_t)c * R + j];
+        const uint32_t root = proot[(size_t)c * R + j];
+        if (cv && root >= a.n) {  // never written by eval_items: record, skip the bit
+          celf_violation(a, 2002u, root, ((uint64_t)c << 32) | j);
+          cv = 0;
+        }
+        const uint32_t word = cv ? (root * R + j) >> 5 : 0xffffffffu;
         const unsigned peers = __match_any_sync(kFull, word);
         if (cv && lane == __ffs(peers) - 1) atomicOr(a.cov + word, peers);
       }
@@ -775,7 +792,12 @@ __device__ __noinline__ int drive_rounds(const CelfArgs &a, CelfSmem &s, uint32_
       for (uint32_t i = tid; i < ncm * R; i += blockDim.x) {
         const uint32_t c = (uint32_t)s.committed[i / R], j = i % R;
         if (pcont[(size_t)c * R + j]) {
-          const uint32_t bit = proot[(size_t)c * R + j] * R + j;
+          const uint32_t root = proot[(size_t)c * R + j];
+          if (root >= a.n) {
+            celf_violation(a, 2002u, root, ((uint64_t)c << 32) | j);
+            continue;
+          }
+          const uint32_t bit = root * R + j;
           atomicOr(a.cov + (bit >> 5), 1u << (bit & 31));
         }
       }
@@ -867,6 +889,10 @@ __global__ void __launch_bounds__(kCelfThreads, 1) k_celf(CelfArgs a) {
   extern __shared__ uint32_t dyn[];
   const int tid = threadIdx.x;
   const bool driver = blockIdx.x == 0;
+  // Helpers: the other blocks of the driver's cluster (none when the launch
+  // has no cluster shape, or clusters of one block; the driver then evaluates
+  // every item itself).
+  const bool helper = !driver && grid.cluster_rank() == 0 && cg::this_cluster().num_blocks() > 1;
   const uint32_t gtid = blockIdx.x * blockDim.x + tid;
   const uint32_t gthreads = gridDim.x * blockDim.x;
   const uint32_t R = a.R;
@@ -993,7 +1019,7 @@ __global__ void __launch_bounds__(kCelfThreads, 1) k_celf(CelfArgs a) {
       }
       __syncthreads();
       if (tid == 0) ctl->cmd = cmd;
-    } else if (POOL_SMEM && blockIdx.x < (unsigned)kEvalCluster) {
+    } else if (POOL_SMEM && helper) {
       helper_rounds(a, s, dyn);
     }
     grid.sync();
@@ -1039,6 +1065,8 @@ cudaError_t launch_celf(const im_graph *g, const im_workspace *ws, const QueryPa
   // round after a refresh commits (its keys are exact); every grid step is
   // followed by at least one round.
   a.round_cap = (uint32_t)(K + 2) * (ra + 8) + 1024;
+  const int64_t rc_ovr = override_value(IM_OVR_CELF_ROUND_CAP);
+  if (rc_ovr > 0 && (uint64_t)rc_ovr < a.round_cap) a.round_cap = (uint32_t)rc_ovr;
   a.g_pool = ws->d_pool;
   a.out_seeds = d_seeds;
   a.out_sigma = d_sigma;
@@ -1058,19 +1086,26 @@ cudaError_t launch_celf(const im_graph *g, const im_workspace *ws, const QueryPa
   // queries running concurrently on other streams; the grid-wide extraction
   // of larger graphs takes every SM.
   int nblocks = (uint32_t)g->n <= kLocalN ? (g->num_sms + 3) / 4 : g->num_sms;
+  if (nblocks > g->num_sms * per_sm) nblocks = g->num_sms * per_sm;
   void *args[] = {&a};
-  if (!a.pool_smem) {
+  // Cluster size of the shared-memory pool launch: kEvalCluster, or a test
+  // override (-1: a plain cooperative launch with no cluster attribute). The
+  // kernel reads the cluster shape it actually received, so every shape
+  // evaluates every (candidate, lane) item.
+  const int64_t c_ovr = override_value(IM_OVR_CELF_CLUSTER);
+  if (!a.pool_smem || c_ovr == -1) {
     dim3 grid(nblocks), block(kCelfThreads);
     return cudaLaunchCooperativeKernel(fn, grid, block, args, dyn, s);
   }
-  // Shared-memory pool: clusters of kEvalCluster blocks (the first cluster
+  const int csize = c_ovr > 0 ? (int)c_ovr : kEvalCluster;
+  // Shared-memory pool: clusters of csize blocks (the driver's cluster
   // evaluates each round's pool together), as many as can be co-resident.
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[2];
   attr[0].id = cudaLaunchAttributeCooperative;
   attr[0].val.cooperative = 1;
   attr[1].id = cudaLaunchAttributeClusterDimension;
-  attr[1].val.clusterDim.x = kEvalCluster;
+  attr[1].val.clusterDim.x = (unsigned)csize;
   attr[1].val.clusterDim.y = 1;
   attr[1].val.clusterDim.z = 1;
   cfg.blockDim = dim3(kCelfThreads);
@@ -1078,14 +1113,14 @@ cudaError_t launch_celf(const im_graph *g, const im_workspace *ws, const QueryPa
   cfg.stream = s;
   cfg.attrs = attr;
   cfg.numAttrs = 2;
-  cfg.gridDim = dim3(kEvalCluster);
+  cfg.gridDim = dim3((unsigned)csize);
   int max_clusters = 0;
   e = cudaOccupancyMaxActiveClusters(&max_clusters, fn, &cfg);
   if (e != cudaSuccess) return e;
   if (max_clusters < 1) return cudaErrorInvalidConfiguration;
-  int nclusters = (nblocks + kEvalCluster - 1) / kEvalCluster;
+  int nclusters = (nblocks + csize - 1) / csize;
   if (nclusters > max_clusters) nclusters = max_clusters;
-  cfg.gridDim = dim3(nclusters * kEvalCluster);
+  cfg.gridDim = dim3((unsigned)(nclusters * csize));
   return cudaLaunchKernelExC(&cfg, fn, args);
 }
 

@@ -185,6 +185,16 @@ struct im_workspace {
 
 namespace imgb {
 
+// ------------------------------------------------------------------ test overrides
+// Process-wide values set by im_debug_override (IM_OVR_* keys; 0 keeps the
+// library's own choice). Read on the host when a kernel is launched.
+int64_t override_value(int key);
+// Every device allocation of the library goes through this gate, so that a
+// test can make the k-th one fail (IM_OVR_FAIL_ALLOC) as cudaMalloc would.
+cudaError_t dev_malloc(void **p, size_t bytes);
+// Union-find walk budget of a launch (uf_cap, or a smaller test override).
+uint32_t uf_budget(uint32_t n);
+
 // ------------------------------------------------------------------ launchers
 // All launchers queue work on `s` and return the launch error (if any).
 cudaError_t launch_prep(const im_workspace *ws, const QueryParams &q, bool init_table,

@@ -121,10 +121,10 @@ int graph_build_device(im_graph *g, const int32_t *h_xadj, const int32_t *h_adj,
   std::vector<int32_t> up, off;
   int64_t m_up = 0;
   const int wblocks = g->num_sms * 8;  // 256-thread blocks, warp per vertex
-  GB_CUDA(cudaMalloc(&g->d_xadj, sizeof(int32_t) * (size_t)(n + 1)), "cudaMalloc xadj");
-  GB_CUDA(cudaMalloc(&g->d_adj, sizeof(int32_t) * (size_t)(arcs > 0 ? arcs : 1)), "cudaMalloc adj");
-  GB_CUDA(cudaMalloc(&d_flags, sizeof(uint32_t)), "cudaMalloc flags");
-  GB_CUDA(cudaMalloc(&d_up, sizeof(int32_t) * (size_t)n), "cudaMalloc counts");
+  GB_CUDA(dev_malloc(reinterpret_cast<void **>(&g->d_xadj), sizeof(int32_t) * (size_t)(n + 1)), "cudaMalloc xadj");
+  GB_CUDA(dev_malloc(reinterpret_cast<void **>(&g->d_adj), sizeof(int32_t) * (size_t)(arcs > 0 ? arcs : 1)), "cudaMalloc adj");
+  GB_CUDA(dev_malloc(reinterpret_cast<void **>(&d_flags), sizeof(uint32_t)), "cudaMalloc flags");
+  GB_CUDA(dev_malloc(reinterpret_cast<void **>(&d_up), sizeof(int32_t) * (size_t)n), "cudaMalloc counts");
   GB_CUDA(cudaMemcpy(g->d_xadj, h_xadj, sizeof(int32_t) * (size_t)(n + 1), cudaMemcpyHostToDevice),
           "copy xadj");
   if (arcs > 0)
@@ -170,8 +170,8 @@ int graph_build_device(im_graph *g, const int32_t *h_xadj, const int32_t *h_adj,
   if (m_up > 0) {
     GB_CUDA(cudaMemcpy(d_up, off.data(), sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice),
             "copy offsets");
-    GB_CUDA(cudaMalloc(&g->d_eu, sizeof(int32_t) * (size_t)m_up), "cudaMalloc eu");
-    GB_CUDA(cudaMalloc(&g->d_ev, sizeof(int32_t) * (size_t)m_up), "cudaMalloc ev");
+    GB_CUDA(dev_malloc(reinterpret_cast<void **>(&g->d_eu), sizeof(int32_t) * (size_t)m_up), "cudaMalloc eu");
+    GB_CUDA(dev_malloc(reinterpret_cast<void **>(&g->d_ev), sizeof(int32_t) * (size_t)m_up), "cudaMalloc ev");
     k_scatter_upper<<<wblocks, 256>>>(g->d_xadj, g->d_adj, n, d_up, g->d_eu, g->d_ev);
     GB_CUDA(cudaGetLastError(), "k_scatter_upper");
   }

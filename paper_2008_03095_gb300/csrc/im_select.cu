@@ -295,7 +295,7 @@ cudaError_t launch_union(const im_graph *g, const im_workspace *ws, const QueryP
   a.T32 = q.T32;
   a.all_live = q.all_live;
   a.R = q.R;
-  a.cap = uf_cap((uint32_t)g->n);
+  a.cap = uf_budget((uint32_t)g->n);
   a.P = ws->d_P;
   a.status = ws->d_status;
   a.mask = d_mask;
@@ -422,7 +422,7 @@ cudaError_t launch_compress(const im_graph *g, const im_workspace *ws, const Que
   if (blocks > cap) blocks = cap;
   if (blocks == 0) blocks = 1;
   k_compress<<<(unsigned)blocks, 256, 0, s>>>(ws->d_P, (uint32_t)g->n, q.R, ws->d_status,
-                                              uf_cap((uint32_t)g->n));
+                                              uf_budget((uint32_t)g->n));
   return cudaGetLastError();
 }
 

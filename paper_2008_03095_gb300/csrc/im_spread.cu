@@ -46,6 +46,7 @@ struct SpreadArgs {
   uint64_t *out;
   int32_t *status;
   unsigned long long *stats;
+  uint32_t level_cap;    // budget of BFS levels (a BFS has at most n levels)
 };
 
 template <class T>
@@ -146,7 +147,7 @@ __global__ void __launch_bounds__(512) k_spread(SpreadArgs a) {
 
   const bool row_in_regs = W <= 64;
   uint32_t level = 0;
-  for (; level < a.n + 2; ++level) {
+  for (; level < a.level_cap; ++level) {
     const uint32_t cc = __ldcg(a.cntlev + level);
     if (cc == 0) break;
     const uint32_t nq = __ldcg(a.chklev + level);
@@ -276,7 +277,7 @@ __global__ void __launch_bounds__(512) k_spread(SpreadArgs a) {
     }
     grid.sync();
   }
-  if (level >= a.n + 2 && tid == 0) set_status(a.status, IM_ETIMEOUT);
+  if (level >= a.level_cap && tid == 0) set_status(a.status, IM_ETIMEOUT);
 #pragma unroll
   for (int d = 16; d > 0; d >>= 1) local += __shfl_xor_sync(kFull, local, d);
   if (lane == 0 && local) atomicAdd(a.acc, local);
@@ -322,6 +323,9 @@ cudaError_t launch_spread(const im_graph *g, const im_workspace *ws, const Query
   a.out = d_sigma;
   a.status = ws->d_status;
   a.stats = ws->d_stats;
+  a.level_cap = (uint32_t)g->n + 2u;
+  const int64_t lo = override_value(IM_OVR_SPREAD_LEVEL_CAP);
+  if (lo > 0 && (uint64_t)lo < a.level_cap) a.level_cap = (uint32_t)lo;
   a.xs_smem = (!d_mask && q.R <= kSpreadSmemLanes) ? 1 : 0;
   const size_t smem = a.xs_smem ? (size_t)q.R * sizeof(uint32_t) : 0;
   int per_sm = 0;

@@ -76,3 +76,13 @@ def test_queries_reject_null_handles(L):
     assert L.im_debug_edge_hash(None, None, 0, None) == im.IM_OK
     assert L.im_debug_edge_hash(None, None, -1, None) == im.IM_EINVAL
     assert L.im_debug_lane_randoms(0, 1, None) == im.IM_EINVAL
+
+
+def test_override_arguments_are_checked(L):
+    for key, val in ((99, 1), (-1, 0), (im.IM_OVR_CELF_CLUSTER, 3), (im.IM_OVR_CELF_CLUSTER, 16),
+                     (im.IM_OVR_UF_CAP, -2), (im.IM_OVR_FAIL_ALLOC, -1)):
+        with pytest.raises(im.IMError) as e:
+            im.im_debug_override(key, val)
+        assert e.value.code == im.IM_EINVAL
+    for key in range(im.IM_NUM_OVERRIDES):
+        im.im_debug_override(key, 0)
