@@ -16,13 +16,29 @@ import numpy as np
 
 from . import build as _build
 
-_lib = None
+_libs = {}
+_variant = "single"
+
+
+def use_all_cores(on: bool = True):
+    """Switch every following call to the OpenMP build (all host cores, or
+    OMP_NUM_THREADS) or back to the single-threaded default. Both builds give
+    identical results."""
+    global _variant
+    _variant = "omp" if on else "single"
+
+
+def threads():
+    """Threads the current build uses (1 for the single-threaded build)."""
+    if _variant != "omp":
+        return 1
+    return int(lib().orc_max_threads())
 
 
 def lib():
-    global _lib
-    if _lib is None:
-        path = _build.build()
+    L = _libs.get(_variant)
+    if L is None:
+        path = _build.build_omp() if _variant == "omp" else _build.build()
         L = ctypes.CDLL(path)
         i32, i64, u32, u64, f64 = (ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32,
                                    ctypes.c_uint64, ctypes.c_double)
@@ -57,8 +73,10 @@ def lib():
         L.orc_select_seeds_masked.restype = i32
         L.orc_estimate_spread_masked.argtypes = [i32, i64, P, P, P, i32, i32, P, P]
         L.orc_estimate_spread_masked.restype = i32
-        _lib = L
-    return _lib
+        L.orc_max_threads.argtypes = []
+        L.orc_max_threads.restype = i32
+        _libs[_variant] = L
+    return L
 
 
 def _p(a):

@@ -6,7 +6,8 @@
 // this file: only the test suite, the package smoke check and the benchmark's
 // CPU-baseline leg use it. It shares no code, header, table or constant
 // generator with the CUDA library; it is a slow, literal restatement of the
-// method's definitions, single-threaded, in the paper's order and notation.
+// method's definitions, single-threaded by default, in the paper's order and
+// notation.
 //
 // What it computes (all integer, exact):
 //   * h(u,v): MurmurHash3_x86_32 of the 8-byte key min(u,v) || max(u,v),
@@ -32,9 +33,21 @@
 // A second sampler takes an explicit per-arc, per-simulation live mask instead
 // of the hash, so that the worked example of Figures 3-4 and brute-force
 // enumerations over all live-edge subsets can be fed in directly.
+//
+// Built with -fopenmp (oracle/_build/liboracle_omp.so, the all-core CPU
+// baseline and the writer of stored expected values for the largest graphs),
+// the simulations of the label pass and the vertices of each greedy step are
+// split over threads. Nothing else changes: every simulation is still labelled
+// by the same BFS, and a greedy step still takes the largest gain with the
+// lowest id among equal gains (each thread keeps its own first maximum, and the
+// thread maxima are compared in id order), so both builds return identical
+// results; only the order of integer additions differs.
 
 #include <algorithm>
 #include <cmath>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <cstdint>
 #include <cstring>
 #include <random>
@@ -187,13 +200,17 @@ void label_one_sample(int32_t n, const int32_t *xadj, const int32_t *adj, const 
 template <class S>
 void all_labels(int32_t n, const int32_t *xadj, const int32_t *adj, int32_t R, const S &smp,
                 int32_t *labels, uint32_t *sizes) {
-  std::vector<int32_t> lab(n), queue(n);
-  std::vector<uint32_t> cnt(n);
-  for (int32_t r = 0; r < R; ++r) {
-    label_one_sample(n, xadj, adj, smp, r, lab, cnt, queue);
-    for (int32_t v = 0; v < n; ++v) {
-      labels[(int64_t)v * R + r] = lab[v];
-      sizes[(int64_t)v * R + r] = cnt[v];
+#pragma omp parallel
+  {
+    std::vector<int32_t> lab(n), queue(n);
+    std::vector<uint32_t> cnt(n);
+#pragma omp for schedule(dynamic, 1)
+    for (int32_t r = 0; r < R; ++r) {
+      label_one_sample(n, xadj, adj, smp, r, lab, cnt, queue);
+      for (int32_t v = 0; v < n; ++v) {
+        labels[(int64_t)v * R + r] = lab[v];
+        sizes[(int64_t)v * R + r] = cnt[v];
+      }
     }
   }
 }
@@ -208,16 +225,28 @@ void greedy(int32_t n, int32_t R, const int32_t *labels, const uint32_t *sizes, 
   for (int32_t k = 0; k < K; ++k) {
     int64_t best = -1;
     uint64_t best_gain = 0;
-    for (int32_t v = 0; v < n; ++v) {
-      if (chosen[v]) continue;
-      uint64_t g = 0;
-      for (int32_t r = 0; r < R; ++r) {
-        int64_t l = labels[(int64_t)v * R + r];
-        if (!cov[l * R + r]) g += sizes[l * R + r];
+#pragma omp parallel
+    {
+      // each thread scans a contiguous id range in increasing order
+      int64_t tbest = -1;
+      uint64_t tgain = 0;
+#pragma omp for schedule(static)
+      for (int32_t v = 0; v < n; ++v) {
+        if (chosen[v]) continue;
+        uint64_t g = 0;
+        for (int32_t r = 0; r < R; ++r) {
+          int64_t l = labels[(int64_t)v * R + r];
+          if (!cov[l * R + r]) g += sizes[l * R + r];
+        }
+        if (tbest < 0 || g > tgain) {  // strict: lowest id wins ties
+          tbest = v;
+          tgain = g;
+        }
       }
-      if (best < 0 || g > best_gain) {  // strict: lowest id wins ties
-        best = v;
-        best_gain = g;
+#pragma omp critical
+      if (tbest >= 0 && (best < 0 || tgain > best_gain || (tgain == best_gain && tbest < best))) {
+        best = tbest;
+        best_gain = tgain;
       }
     }
     int32_t s = (int32_t)best;
@@ -292,6 +321,15 @@ void orc_mt19937(uint32_t seed, int64_t count, uint32_t *out) {
 }
 
 uint64_t orc_threshold(double p) { return threshold(p); }
+
+// Threads a parallel region of this build uses (1 without OpenMP).
+int32_t orc_max_threads(void) {
+#ifdef _OPENMP
+  return (int32_t)omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
 
 int32_t orc_live(int32_t u, int32_t v, uint32_t x, double p) {
   return (uint64_t)(x ^ edge_hash(u, v)) < threshold(p) ? 1 : 0;

@@ -9,13 +9,20 @@ on one stream).
   every prefix of the selected seeds equals sigma*R of that prefix.
 - clustered_n334863 and powerlaw_n4m (label tables of 2.7 and 8.2 GB): labels
   and sizes of sampled simulations equal the oracle's bit for bit, and the
-  selection satisfies properties that hold at any size, checked with the spread
-  kernel, which shares no code with the lazy greedy:
+  whole seed sequence and sigma*R equal the oracle's, stored by
+  tests/golden/make_oracle_expected.py (which runs only the oracle) together
+  with the SHA-256 of the graph it ran on. These graphs take the grid-wide
+  prefix extraction of the lazy greedy. The selection also satisfies
+  properties that hold at any size, checked with the spread kernel, which
+  shares no code with the lazy greedy:
     * sigma*R of every checked prefix equals the spread estimate of that prefix;
     * the first seed's gain equals the spread of the first seed alone;
     * at checked steps no sampled competitor has a larger marginal gain, and on
       equal gain the chosen id is the lower one (greedy with lowest-id ties).
 """
+import os
+import sys
+
 import numpy as np
 import pytest
 
@@ -25,6 +32,20 @@ from paper_2008_03095_gb300 import build as im_build
 from paper_2008_03095_gb300 import synth
 
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+sys.path.insert(0, os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden"))
+from make_graph_digests import digest  # noqa: E402
+from make_oracle_expected import read_expected  # noqa: E402
+
+EXPECTED = read_expected()
+
+
+def _stored_oracle_match(name, xadj, adj, w, p, seeds, sigma):
+    sha, K, R, seed, oseeds, osigma = EXPECTED[(name, p)]
+    assert (K, R, seed) == (w["K"], w["R"], w["rng_seed"])
+    assert digest(xadj, adj) == sha, "the generator produced a different graph"
+    assert np.array_equal(seeds, oseeds), (seeds, oseeds)
+    assert np.array_equal(sigma, osigma), (sigma, osigma)
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -101,18 +122,19 @@ def test_powerlaw_n37154_full_parity(p):
 
 
 @pytest.mark.parametrize("p", [0.01, 0.05])
-def test_clustered_n334863_sampled_parity_and_greedy_properties(p):
+def test_clustered_n334863_full_parity_with_stored_oracle(p):
     name = "clustered_n334863"
     w = synth.WORKLOADS[name]
     xadj, adj = synth.workload_graph(name)
     g = im.im_graph_create(xadj, adj)
     _sampled_lanes_match(g, xadj, adj, w, p, [0, 5, 1500, 2047])
     seeds, sigma, spread = _select_like_bench(g, w, p)
+    _stored_oracle_match(name, xadj, adj, w, p, seeds, sigma)
     _greedy_properties(g, xadj, w, p, seeds, sigma, spread, np.random.default_rng(4))
     g.close()
 
 
-def test_powerlaw_n4m_sampled_parity_and_greedy_properties():
+def test_powerlaw_n4m_full_parity_with_stored_oracle():
     name = "powerlaw_n4m"
     w = synth.WORKLOADS[name]
     xadj, adj = synth.workload_graph(name)
@@ -120,6 +142,7 @@ def test_powerlaw_n4m_sampled_parity_and_greedy_properties():
     p = w["ps"][0]
     _sampled_lanes_match(g, xadj, adj, w, p, [0, 511])
     seeds, sigma, spread = _select_like_bench(g, w, p)
+    _stored_oracle_match(name, xadj, adj, w, p, seeds, sigma)
     _greedy_properties(g, xadj, w, p, seeds, sigma, spread, np.random.default_rng(41))
     g.close()
 

@@ -384,3 +384,48 @@ def test_lane_sharding_invariance_of_gains_and_greedy(p):
         total += int(g[best])
         assert seeds[k] == best and int(sigma[k]) == total
         S.append(best)
+
+
+# ------------------------------------------------------------------ OpenMP build
+
+
+@pytest.mark.parametrize("mk,K,R,p", [
+    (lambda: synth.chung_lu(3000, 12000, 2.2, 21), 20, 96, 0.05),
+    (lambda: synth.random_graph(400, 1600, 22), 30, 33, 0.3),
+    (lambda: synth.chung_lu(1500, 9000, 2.1, 23), 15, 256, 0.0),
+])
+def test_all_core_build_gives_identical_results(mk, K, R, p):
+    """The OpenMP build (all-core CPU baseline, writer of the stored expected
+    values) splits simulations and greedy candidates over threads; ties must
+    still go to the lowest id, so its output equals the single-threaded one."""
+    xadj, adj = mk()
+    want = oracle.select_seeds(xadj, adj, K, R, p, 7)
+    wlab = oracle.labels(xadj, adj, R, p, 7)
+    oracle.use_all_cores(True)
+    try:
+        assert oracle.threads() >= 1
+        got = oracle.select_seeds(xadj, adj, K, R, p, 7)
+        glab = oracle.labels(xadj, adj, R, p, 7)
+    finally:
+        oracle.use_all_cores(False)
+    assert np.array_equal(got[0], want[0]) and np.array_equal(got[1], want[1])
+    assert np.array_equal(glab[0], wlab[0]) and np.array_equal(glab[1], wlab[1])
+
+
+def test_stored_expected_values_match_the_committed_graph_digests():
+    """Rows of tests/golden/oracle_expected_seeds.txt name the graph they ran
+    on; the digests must be the committed ones, K and R the workload's, and
+    sigma*R a non-decreasing sequence with positive first entry."""
+    import sys
+    sys.path.insert(0, _util.GOLDEN)
+    from make_oracle_expected import read_expected
+
+    digests = {row[0]: row[4] for row in _util.golden_lines("graph_sha256.txt")}
+    exp = read_expected()
+    assert {k[0] for k in exp} >= {"clustered_n334863", "powerlaw_n4m"}
+    for (name, p), (sha, K, R, seed, seeds, sigma) in exp.items():
+        w = synth.WORKLOADS[name]
+        assert sha == digests[name]
+        assert (K, R, seed) == (w["K"], w["R"], w["rng_seed"]) and p in w["ps"]
+        assert len(set(seeds.tolist())) == K and len(sigma) == K
+        assert sigma[0] > 0 and np.all(np.diff(sigma.astype(np.int64)) >= 0)
