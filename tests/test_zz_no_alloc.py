@@ -69,3 +69,55 @@ def test_limits_are_rejected_before_device_work():
     assert e.value.code == im.IM_EINVAL
     # the library stays usable afterwards
     assert im.im_estimate_spread_noalloc(g, [1], 8, 0.1, 7) == im.im_estimate_spread(g, [1], 8, 0.1, 7)
+
+
+def test_calls_leave_free_device_memory_unchanged():
+    """The property the entry point exists for: once the static region is in
+    place (first call), further calls take no device memory at all."""
+    import torch
+
+    xadj, adj = synth.chung_lu(2000, 8000, 2.5, 1)
+    g = _graph(xadj, adj)
+    S = np.array([1, 2, 3, 500], dtype=np.int32)
+    want = im.im_estimate_spread(g, S, 128, 0.05, 7)  # the allocating path, first
+    assert im.im_estimate_spread_noalloc(g, S, 128, 0.05, 7) == want  # warm-up call
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for R in (1, 64, 128, LIM["IM_NOALLOC_MAX_R"]):
+        im.im_estimate_spread_noalloc(g, S, R, 0.05, 7)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    g.close()
+
+
+def test_succeeds_while_another_allocator_holds_the_free_memory():
+    """A caching allocator that has taken almost all free device memory leaves
+    the allocating entry point nothing to work with, but not this one."""
+    import torch
+
+    xadj, adj = synth.chung_lu(2000, 8000, 2.5, 1)
+    g = _graph(xadj, adj)
+    S = np.array([7, 8, 9], dtype=np.int32)
+    want = im.im_estimate_spread(g, S, 256, 0.02, 7)
+    assert im.im_estimate_spread_noalloc(g, S, 256, 0.02, 7) == want
+    torch.cuda.synchronize()
+    hog = None
+    try:
+        free = torch.cuda.mem_get_info()[0]
+        # leave 256 MiB for the driver (kernel launches, local memory)
+        hog = torch.empty(max(free - (256 << 20), 0), dtype=torch.uint8, device="cuda")
+        g2 = None
+        for _ in range(3):
+            assert im.im_estimate_spread_noalloc(g, S, 256, 0.02, 7) == want
+        # a fresh graph's allocating query needs a workspace larger than what is left
+        xb, ab = synth.chung_lu(30000, 200000, 2.3, 5)
+        g2 = _graph(xb, ab) if torch.cuda.mem_get_info()[0] > (64 << 20) else None
+        if g2 is not None:
+            with pytest.raises(im.IMError) as e:
+                im.im_estimate_spread(g2, [0], 65536, 0.02, 7)  # n*R*4 = 7.9 GB of workspace
+            assert e.value.code == im.IM_ENOMEM
+            g2.close()
+    finally:
+        del hog
+        torch.cuda.empty_cache()
+    g.close()
