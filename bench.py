@@ -1,18 +1,20 @@
 #!/usr/bin/env python
 """Benchmark of the fused-sampling influence-maximization hot path on one GB300.
 
-Workload (default): undirected power-law graph n=15,233, m=58,891 (exponent
-2.3, max degree ~350; NetHEP shape), R=1024 simulations, K=50 seeds,
-p in {0.005, 0.01, 0.05}, X_r from MT19937(7). One step = for each p, select
-K seeds (all phases of the hot path: lane randoms, fused hash-sample +
-components, size memo, first gains, CELF) and estimate the spread of the
-selected set. Units: sampled edge visits, 2m*R per query (every arc in every
-simulation counted once); value = units / time in GTEPS x R.
+Workload (default, the largest single-GPU configuration): undirected
+power-law Chung-Lu graph n=4,000,000, m=35,000,000 (exponent 2.2), R=512
+simulations, K=50 seeds, p=0.01, X_r from MT19937(7). One step = select K
+seeds (every phase of the hot path: lane randoms, fused hash-sample +
+components, size memo, first gains, lazy greedy) and estimate the spread of
+the selected set. Units: sampled edge visits, 2m*R per query (every arc in
+every simulation counted once); value = units / time in GTEPS x R. The
+label table (8.2 GB) is far larger than L2, so no flush is needed between
+steps; a 256 MiB write flushes it anyway.
 
-Timing: CUDA events on the launching stream around each step; the L2 cache is
-flushed (256 MiB write) between steps, outside the timed intervals; W warm-up
-steps; K timed steps; max over ranks. `--impl reference` times the CPU oracle
-on a bounded sample of the same workload instead.
+Timing: CUDA events on the launching stream around each step; W warm-up
+steps; K timed steps; max over ranks. Two more workloads are measured the same
+way with fewer steps and reported under `extra_workloads`. `--impl reference`
+times the CPU oracle on a bounded sample of the same workload instead.
 """
 import argparse
 import json
@@ -31,11 +33,23 @@ if ROOT not in sys.path:
 
 METRIC = "K-seed selection wall time + sampled edge-visits/s (GTEPS×R), % HBM peak"
 UNIT = "GTEPS×R"
-WORKLOAD = "powerlaw_n15233"
-REF_R = 64  # lanes per query in a reference-arm (CPU oracle) step
+WORKLOAD = "powerlaw_n4m"
+EXTRA_WORKLOADS = ("clustered_n334863", "powerlaw_n15233")
+# Simulations of one oracle step: the reference arm (every timed step) and the
+# CPU baseline (one step per build), a prefix X_0..X_{r-1} of the workload's R.
+REF_LANES = {"powerlaw_n4m": 1, "clustered_n334863": 8, "powerlaw_n37154": 16,
+             "powerlaw_n15233": 64, "powerlaw_n2000": 256}
+CPU_LANES = {"powerlaw_n4m": (2, 16), "clustered_n334863": (32, 256),
+             "powerlaw_n37154": (64, 512), "powerlaw_n15233": (256, 1024),
+             "powerlaw_n2000": (256, 256)}  # (single thread, all cores)
+# Workloads whose oracle step is select_seeds alone: every oracle call first
+# validates the CSR (about 10 s at 70M arcs), so select + spread would double
+# the step; leaving out the spread only makes the oracle's rate look better.
+ORACLE_SELECT_ONLY = ("powerlaw_n4m",)
+FLUSH_BYTES = 256 << 20
 
 
-def parse_args():
+def parse_args(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
@@ -43,8 +57,10 @@ def parse_args():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=5)
-    return ap.parse_args()
+    ap.add_argument("--extra-steps", type=int, default=5)
+    return ap.parse_args(argv)
 
 
 # ------------------------------------------------------------------ helpers
@@ -130,7 +146,7 @@ class ClockSampler:
         except Exception:
             self.proc.kill()
         self.thread.join(timeout=2)
-        sm, smax, reasons = [], [], set()
+        sm, smax, power, reasons = [], [], [], set()
         names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
         for line in self.lines:
             parts = [p.strip() for p in line.split(",")]
@@ -139,6 +155,7 @@ class ClockSampler:
             try:
                 sm.append(float(parts[0]))
                 smax.append(float(parts[1]))
+                power.append(float(parts[2]))
             except ValueError:
                 continue
             for name, val in zip(names, parts[4:8]):
@@ -146,55 +163,85 @@ class ClockSampler:
                     reasons.add(name)
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_max": max(power) if power else None}
+
+
+def workload_config(name, xadj, adj, w, R=None, note=None):
+    deg = np.diff(xadj)
+    R = w["R"] if R is None else R
+    shape = "clustered low-skew" if name.startswith("clustered") else "power-law"
+    cfg = {"workload": "%s: undirected %s graph n=%d m=%d (max degree %d), R=%d, K=%d, "
+                       "p in %s, rng_seed %d" % (name, shape, xadj.shape[0] - 1,
+                                                 adj.shape[0] // 2, int(deg.max()), R, w["K"],
+                                                 list(w["ps"]), w["rng_seed"]),
+           "n": int(xadj.shape[0] - 1), "m": int(adj.shape[0] // 2), "R": R, "K": w["K"],
+           "p": list(w["ps"]), "rng_seed": w["rng_seed"],
+           "l2": "label table larger than L2 (n*R*4 bytes); a 256 MiB device write also "
+                 "flushes L2 between timed steps"}
+    if note:
+        cfg["note"] = note
+    return cfg
+
+
+def stored_oracle(name):
+    """{p: (seeds, sigma)} written by tests/golden/make_oracle_expected.py."""
+    sys.path.insert(0, os.path.join(ROOT, "tests", "golden"))
+    try:
+        from make_oracle_expected import read_expected
+    except Exception:
+        return {}
+    return {p: (v[4], v[5]) for (n, p), v in read_expected().items() if n == name}
 
 
 # ------------------------------------------------------------------ reference arm
 
 
+def oracle_step(oracle, xadj, adj, w, lanes, spread=True):
+    for p in w["ps"]:
+        seeds, sigma = oracle.select_seeds(xadj, adj, w["K"], lanes, p, w["rng_seed"])
+        if spread:
+            oracle.estimate_spread(xadj, adj, seeds, lanes, p, w["rng_seed"])
+
+
+def oracle_step_kind(name):
+    return ("select_seeds" if name in ORACLE_SELECT_ONLY
+            else "select_seeds + estimate_spread")
+
+
 def run_reference(args, xadj, adj, w):
-    """The CPU oracle on a bounded sample of the workload (REF_R lanes per query)."""
+    """The CPU oracle, single-threaded as it stands, on a bounded sample of
+    the workload: every step selects K seeds and estimates their spread on
+    the first REF_LANES simulations of the workload's R."""
     import oracle
 
     m = adj.shape[0] // 2
-    ps = w["ps"]
-
-    def step():
-        for p in ps:
-            seeds, sigma = oracle.select_seeds(xadj, adj, w["K"], REF_R, p, w["rng_seed"])
-            oracle.estimate_spread(xadj, adj, seeds, REF_R, p, w["rng_seed"])
-
+    lanes = REF_LANES.get(args.workload, 8)
+    spread = args.workload not in ORACLE_SELECT_ONLY
     for _ in range(args.warmup):
-        step()
+        oracle_step(oracle, xadj, adj, w, lanes, spread)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        step()
+        oracle_step(oracle, xadj, adj, w, lanes, spread)
     dt = time.perf_counter() - t0
-    units = len(ps) * 2 * m * REF_R * args.steps
+    units = len(w["ps"]) * 2 * m * lanes * args.steps
     value = units / dt / 1e9
-    sample = ("oracle select_seeds + estimate_spread, K=%d, %d lanes per query (of R=%d), p in %s"
-              % (w["K"], REF_R, w["R"], list(ps)))
+    sample = ("oracle %s, K=%d, the first %d of the workload's R=%d simulations, p in %s, "
+              "per step" % (oracle_step_kind(args.workload), w["K"], lanes, w["R"],
+                            list(w["ps"])))
     return {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": workload_config(args.workload, xadj, adj, w),
+        "config": workload_config(args.workload, xadj, adj, w, R=lanes,
+                                  note="R=%d sampled of the workload's %d; the metric is per "
+                                       "sampled edge visit, so it compares across R"
+                                       % (lanes, w["R"])),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": sample, "cpu": cpu_model()},
+                         "sample": sample, "cpu": cpu_model(), "nproc": os.cpu_count()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
-
-
-def workload_config(name, xadj, adj, w):
-    deg = np.diff(xadj)
-    return {"workload": "%s: undirected power-law graph n=%d m=%d (max degree %d), R=%d, K=%d, "
-                        "p in %s, rng_seed %d" % (name, xadj.shape[0] - 1, adj.shape[0] // 2,
-                                                  int(deg.max()), w["R"], w["K"], list(w["ps"]),
-                                                  w["rng_seed"]),
-            "n": int(xadj.shape[0] - 1), "m": int(adj.shape[0] // 2), "R": w["R"], "K": w["K"],
-            "p": list(w["ps"]), "rng_seed": w["rng_seed"],
-            "l2": "flushed between timed steps (256 MiB device write)"}
 
 
 # ------------------------------------------------------------------ our arm
@@ -215,27 +262,48 @@ def algorithmic_bytes(phase, n, m_up, R, T):
     return None
 
 
-def celf_algorithmic_bytes(n, R, evaluations, extractions, refreshes):
-    """Minimum bytes of one lazy-greedy launch, from its work counters: each
-    exact gain evaluation reads the candidate's R labels, the R root sizes and
-    R covered bits; each prefix extraction scans the n keys; each refresh
-    re-evaluates every vertex (labels, sizes, covered bits) and rewrites the
-    keys."""
-    per_eval = 4 * R + 4 * R + R / 8
-    return (evaluations * per_eval + extractions * 8 * n
-            + refreshes * (n * per_eval + 8 * n))
+def celf_method_bytes(n, R, evaluations, extractions):
+    """Bytes the method itself moves in one lazy-greedy launch (the marginal-
+    gain reduce of Algorithm 7): each exact evaluation reads the candidate's R
+    labels, the R root sizes and R covered bits; each prefix extraction scans
+    the n bounds."""
+    return evaluations * (4 * R + 4 * R + R / 8) + extractions * 8 * n
 
 
-def run_ours(args, xadj, adj, w):
+def celf_refresh_bytes(n, R, refreshes):
+    """Bytes of the dense refreshes (every vertex re-evaluated), a choice of
+    this design rather than work the method requires."""
+    return refreshes * (n * (4 * R + 4 * R + R / 8) + 8 * n)
+
+
+def g_m_up(xadj, adj):
+    n = xadj.shape[0] - 1
+    src = np.repeat(np.arange(n), np.diff(xadj))
+    return int(np.count_nonzero(adj > src))
+
+
+def committed_traffic(kernel, workload):
+    """DRAM bytes per launch from a committed ncu summary (profiles/dram_traffic.txt)."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        for line in f:
+            parts = line.split()
+            if len(parts) >= 3 and not line.startswith("#") and parts[0] == kernel \
+                    and parts[1] == workload:
+                return float(parts[2])
+    return None
+
+
+def measure(name, w, xadj, adj, steps, warmup, world, detail):
+    """Device-timed steps of one workload (inputs resident). Returns the
+    record and, when detail is set, the per-kernel breakdown."""
     import torch
 
     import paper_2008_03095_gb300 as im
-    from paper_2008_03095_gb300 import build as lib_build
 
-    rank, world, local_rank = dist_env()
-    lib_build.build()
-    im.lib()
-    torch.cuda.set_device(local_rank)
+    rank, _, local_rank = dist_env()
     dev = torch.device("cuda", local_rank)
     n = xadj.shape[0] - 1
     m = adj.shape[0] // 2
@@ -244,15 +312,15 @@ def run_ours(args, xadj, adj, w):
     im.im_set_stream(stream)
 
     g = im.im_graph_create(xadj, adj)
-    ws = im.im_workspace_create(g, R)
     d_seeds = torch.empty((len(ps), K), dtype=torch.int32, device=dev)
     d_sigma = torch.empty((len(ps), K), dtype=torch.int64, device=dev)
     d_spread = torch.empty((len(ps),), dtype=torch.int64, device=dev)
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
     # The queries of a step are independent: each runs on its own stream with
     # its own workspace, forked from and joined back to the launching stream.
     q_streams = [torch.cuda.Stream(device=dev) for _ in ps]
-    q_ws = [ws] + [im.im_workspace_create(g, R) for _ in ps[1:]]
+    q_ws = [im.im_workspace_create(g, R) for _ in ps]
+    ws = q_ws[0]
 
     def step():
         fork = torch.cuda.Event()
@@ -276,12 +344,6 @@ def run_ours(args, xadj, adj, w):
             im.im_select_seeds_async(g, ws, K, R, p, seed, d_seeds[i], d_sigma[i])
             im.im_estimate_spread_async(g, ws, d_seeds[i], K, R, p, seed, d_spread[i:i + 1])
 
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    for w_ in q_ws:
-        im.im_workspace_status(w_)
-
     def timed_steps(nsteps, fn=step):
         starts = [torch.cuda.Event(enable_timing=True) for _ in range(nsteps)]
         ends = [torch.cuda.Event(enable_timing=True) for _ in range(nsteps)]
@@ -293,15 +355,22 @@ def run_ours(args, xadj, adj, w):
         torch.cuda.synchronize()
         return sum(s.elapsed_time(e) for s, e in zip(starts, ends))
 
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    for w_ in q_ws:
+        im.im_workspace_status(w_)
+
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    clocks = ClockSampler(local_rank)
-    clocks.start()
+    clocks = ClockSampler(local_rank) if detail else None
+    if clocks:
+        clocks.start()
     launches0 = im.im_kernel_launches()
-    total_ms = timed_steps(args.steps)
+    total_ms = timed_steps(steps)
     launches = im.im_kernel_launches() - launches0
-    clock_info = clocks.stop()
+    clock_info = clocks.stop() if clocks else None
     for w_ in q_ws:
         im.im_workspace_status(w_)
     if world > 1:
@@ -315,123 +384,121 @@ def run_ours(args, xadj, adj, w):
 
     # Per-kernel times: the same steps again with events around every launch,
     # then each p on its own (kernel times and device work counters per query).
+    nprof = max(1, min(steps, 10))
     im.im_workspace_stats(ws)
     im.im_profile_enable(True)
-    serial_ms = timed_steps(args.steps, step_serial)
+    serial_ms = timed_steps(nprof, step_serial)
     prof = im.im_profile_read()
     by_p = {}
     for i, p in enumerate(ps):
         im.im_profile_read()
         im.im_workspace_stats(ws)
-        for _ in range(args.steps):
+        for _ in range(nprof):
             flush.zero_()
             im.im_select_seeds_async(g, ws, K, R, p, seed, d_seeds[i], d_sigma[i])
             im.im_estimate_spread_async(g, ws, d_seeds[i], K, R, p, seed, d_spread[i:i + 1])
         pp = im.im_profile_read()
         st = im.im_workspace_stats(ws)
         by_p[str(p)] = {"avg_us": {k: round(v[0] / v[1] * 1e3, 2) for k, v in pp.items() if v[1]},
-                        "per_query": {k: v / args.steps for k, v in st.items()}}
+                        "per_query": {k: v / nprof for k, v in st.items()}}
     im.im_profile_enable(False)
+    im.im_set_stream(None)
+    for w_ in q_ws:
+        w_.close()
+    g.close()
+    del flush
+    torch.cuda.empty_cache()
 
+    peak, peak_kind = measured_peaks()
     units_per_step = len(ps) * 2 * m * R
-    value = job_throughput(units_per_step * args.steps, total_ms / 1e3, world)
+    rec = {"ms_per_step": total_ms / steps, "steps": steps, "warmup": warmup,
+           "value": job_throughput(units_per_step * steps, total_ms / 1e3, world),
+           "ms_per_step_one_stream": serial_ms / nprof, "gpu_launches": int(launches),
+           "consistent_spread": consistent}
+    expected = stored_oracle(name)
+    if expected:
+        rec["parity_vs_stored_oracle"] = bool(all(
+            p in expected and np.array_equal(seeds_h[i], expected[p][0])
+            and np.array_equal(sigma_h[i], expected[p][1]) for i, p in enumerate(ps)))
+
+    # The component pipeline (label init, fused sample + union, size memo,
+    # first gains) against its algorithmic floor 8m + 4(n+1) + 20nR bytes per
+    # query: the CSR once, labels written, read for sizes, sizes written,
+    # labels and sizes read for the first gains.
+    cc_phases = ("prep", "union", "compress", "gains")
+    cc_us = sum(prof[ph][0] for ph in cc_phases) * 1e3 / (nprof * len(ps))
+    cc_bytes = 8 * m + 4 * (n + 1) + 20 * n * R
+    cc_gbs = cc_bytes / (cc_us / 1e6) / 1e9
+    rec["component_pipeline"] = {
+        "phases": list(cc_phases), "us_per_query": cc_us, "bytes_per_query": cc_bytes,
+        "achieved_gbs": cc_gbs, "frac": cc_gbs / peak, "peak": peak, "peak_kind": peak_kind,
+        "frac_of": "measured" if peak_kind == "measured" else "fallback"}
     per_kernel = {k: {"total_ms": v[0], "launches": v[1],
                       "avg_us": (v[0] / v[1] * 1e3) if v[1] else None} for k, v in prof.items()}
-    peak, peak_kind = measured_peaks()
-    T = {p: im.im_sampling_threshold(p) for p in ps}
+    tot = sum(v[0] for v in prof.values())
+    for k in per_kernel:
+        per_kernel[k]["share"] = prof[k][0] / tot if tot else None
+    rec["per_kernel"] = per_kernel
+    rec["per_p"] = by_p
+    if not detail:
+        return rec, (seeds_h, sigma_h, spread_h)
+
+    rec["clocks"] = clock_info
+    # Roofline of the dominant kernel (largest share of device time).
     dominant = max(prof, key=lambda k: prof[k][0])
-    roof = None
-    bytes_per_launch = None
-    if dominant in ("prep", "compress", "gains"):
-        bytes_per_launch = algorithmic_bytes(dominant, n, 0, R, 0)
-    elif dominant == "union":
-        bytes_per_launch = statistics.mean(algorithmic_bytes("union", n, g_m_up(xadj, adj), R, T[p])
-                                           for p in ps)
-    note = None
+    T = {p: im.im_sampling_threshold(p) for p in ps}
+    avg_s = prof[dominant][0] / prof[dominant][1] / 1e3
+    roof = {"kernel": "k_" + dominant, "bound": "hbm", "peak": peak, "unit": "GB/s",
+            "peak_kind": peak_kind, "avg_launch_us": avg_s * 1e6,
+            "share_of_device_time": prof[dominant][0] / tot if tot else None}
     if dominant == "celf":
-        # per-launch average over the queries of a step, from the device counters
         q = [by_p[str(p)]["per_query"] for p in ps]
-        bytes_per_launch = statistics.mean(
-            celf_algorithmic_bytes(n, R, x["celf_evaluations"], x["celf_extractions"],
-                                   x["celf_refreshes"]) for x in q)
-        note = ("latency-bound: one block runs the sequential lazy-greedy rounds while the "
-                "grid waits; the HBM roof is reported for its algorithmic bytes")
-    if bytes_per_launch is not None:
-        avg_s = prof[dominant][0] / prof[dominant][1] / 1e3
-        achieved = bytes_per_launch / avg_s / 1e9
-        roof = {"kernel": "k_" + dominant, "bound": "hbm", "achieved": achieved, "peak": peak,
-                "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind,
-                "traffic": committed_traffic("k_" + dominant, args.workload),
-                "bytes_per_launch": bytes_per_launch}
-        if note:
-            roof["note"] = note
+        mb = statistics.mean(celf_method_bytes(n, R, x["celf_evaluations"], x["celf_extractions"])
+                             for x in q)
+        rb = statistics.mean(celf_refresh_bytes(n, R, x["celf_refreshes"]) for x in q)
+        roof.update(bytes_per_launch=mb, refresh_bytes_per_launch=rb,
+                    achieved=mb / avg_s / 1e9,
+                    note="method bytes only (exact gain evaluations E*(8R + R/8) plus prefix "
+                         "extractions X*8n); the dense refreshes' bytes are given apart; "
+                         "latency-bound: the driver's cluster runs the sequential rounds; "
+                         "no DRAM counters: the profiler is not run on this cooperative "
+                         "cluster launch",
+                    traffic=None)
     else:
-        roof = {"kernel": "k_" + dominant, "bound": "latency", "achieved": None, "peak": peak,
-                "unit": "GB/s", "frac": None, "peak_kind": peak_kind, "traffic": None}
-    # the best HBM-bound kernel, reported beside the dominant one
+        if dominant == "union":
+            b = statistics.mean(algorithmic_bytes("union", n, g_m_up(xadj, adj), R, T[p])
+                                for p in ps)
+        else:
+            b = algorithmic_bytes(dominant, n, 0, R, 0)
+        if b is None:  # spread: per-level work varies; report its time only
+            roof.update(bound="latency", achieved=None, bytes_per_launch=None, traffic=None)
+        else:
+            roof.update(bytes_per_launch=b, achieved=b / avg_s / 1e9,
+                        traffic=committed_traffic("k_" + dominant, name))
+    if roof.get("achieved") is not None:
+        roof["frac"] = roof["achieved"] / peak
+        roof["frac_of"] = "measured" if peak_kind == "measured" else "fallback"
+    else:
+        roof["frac"] = None
+    rec["roofline"] = roof
     hbm = {}
     for ph in ("prep", "compress", "gains"):
         if prof[ph][1]:
             b = algorithmic_bytes(ph, n, 0, R, 0)
             a = b / (prof[ph][0] / prof[ph][1] / 1e3) / 1e9
-            hbm["k_" + ph] = {"achieved_gbs": a, "frac": a / peak, "bytes_per_launch": b}
-
-    # The component pipeline (label init, fused sample + union, size memo,
-    # first gains) against its algorithmic floor 8m + 20nR bytes per query:
-    # the CSR once, labels written, read for sizes, sizes written, labels and
-    # sizes read for the first gains.
-    cc_phases = ("prep", "union", "compress", "gains")
-    cc_us = sum(prof[ph][0] / prof[ph][1] * 1e3 for ph in cc_phases if prof[ph][1])
-    cc_bytes = 8 * m + 4 * (n + 1) + 20 * n * R
-    cc_gbs = cc_bytes / (cc_us / 1e6) / 1e9
-    cc = {"phases": list(cc_phases), "us_per_query": cc_us, "bytes_per_query": cc_bytes,
-          "achieved_gbs": cc_gbs, "frac": cc_gbs / peak, "peak": peak, "peak_kind": peak_kind}
-
-    out = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": workload_config(args.workload, xadj, adj, w),
-        "select_plus_spread_ms_per_query": total_ms / args.steps / len(ps),
-        "queries_concurrent": len(ps),
-        "ms_per_step_one_stream": serial_ms / args.steps,
-        "gpu_launches": int(launches), "roofline": roof, "hbm_kernels": hbm,
-        "component_pipeline": cc,
-        "per_kernel": per_kernel, "per_p": by_p, "clocks": clock_info, "consistent_spread": consistent,
-        "paper_context": "NetHEP (15,235 v / 58,892 e), K=50, p=0.01: 0.08 s on 2x Xeon "
-                         "E5-2620v4, 16 threads (Table 4); R not stated",
-    }
-    out["_gpu_results"] = (seeds_h, sigma_h, spread_h)
-    out["_e2e"] = lambda: run_e2e(args, xadj, adj, w, im, torch)
-    for w_ in q_ws:
-        w_.close()
-    g.close()
-    return out
+            hbm["k_" + ph] = {"achieved_gbs": a, "frac": a / peak, "bytes_per_launch": b,
+                              "traffic": committed_traffic("k_" + ph, name)}
+    rec["hbm_kernels"] = hbm
+    return rec, (seeds_h, sigma_h, spread_h)
 
 
-def g_m_up(xadj, adj):
-    n = xadj.shape[0] - 1
-    src = np.repeat(np.arange(n), np.diff(xadj))
-    return int(np.count_nonzero(adj > src))
-
-
-def committed_traffic(kernel, workload):
-    """DRAM bytes per launch from a committed ncu summary (profiles/dram_traffic.txt)."""
-    path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
-    if not os.path.exists(path):
-        return None
-    with open(path) as f:
-        for line in f:
-            parts = line.split()
-            if len(parts) >= 3 and not line.startswith("#") and parts[0] == kernel \
-                    and parts[1] == workload:
-                return float(parts[2])
-    return None
-
-
-def run_e2e(args, xadj, adj, w, im, torch):
+def run_e2e(args, xadj, adj, w, world):
     """Same metric through the blocking C ABI with host buffers: graph upload
     from pinned host memory, select (host outputs), spread (host seeds), free."""
+    import torch
+
+    import paper_2008_03095_gb300 as im
+
     n = xadj.shape[0] - 1
     m = adj.shape[0] // 2
     R, K, ps, seed = w["R"], w["K"], list(w["ps"]), w["rng_seed"]
@@ -457,7 +524,6 @@ def run_e2e(args, xadj, adj, w, im, torch):
         step()
     torch.cuda.synchronize()
     dt = max_over_ranks(time.perf_counter() - t0, torch.device("cuda", torch.cuda.current_device()))
-    world = torch.distributed.get_world_size() if torch.distributed.is_initialized() else 1
     units = len(ps) * 2 * m * R * args.e2e_steps
     h2d = 4 * (n + 1) + 8 * m + len(ps) * K * 4
     d2h = len(ps) * (K * 4 + K * 8 + 8)
@@ -468,35 +534,89 @@ def run_e2e(args, xadj, adj, w, im, torch):
                     "per p + im_graph_destroy"}
 
 
-def run_cpu_baseline(xadj, adj, w, gpu_results):
-    """The oracle, as it stands, single-threaded, on one full step of the workload."""
+def run_cpu_baseline(name, xadj, adj, w):
+    """The oracle as it stands on the host cores: single-threaded and its
+    OpenMP build on all cores, each on one step of the workload restricted to
+    the first few simulations (CPU_LANES), scaled per sampled edge visit."""
     import oracle
 
     m = adj.shape[0] // 2
-    R, K, ps, seed = w["R"], w["K"], list(w["ps"]), w["rng_seed"]
-    seeds_g, sigma_g, spread_g = gpu_results
-    parity = True
-    t0 = time.perf_counter()
-    for i, p in enumerate(ps):
-        s, sg = oracle.select_seeds(xadj, adj, K, R, p, seed)
-        sp = oracle.estimate_spread(xadj, adj, s, R, p, seed)
-        parity &= bool(np.array_equal(s, seeds_g[i]) and np.array_equal(sg, sigma_g[i])
-                       and sp == int(spread_g[i]))
-    dt = time.perf_counter() - t0
-    return {"value": len(ps) * 2 * m * R / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "one full step (select K=%d + spread, R=%d, p in %s), single thread"
-                      % (K, R, ps), "seconds": dt, "cpu": cpu_model()}, parity
+    l1, lall = CPU_LANES.get(name, (8, 64))
+    out = {}
+    spread = name not in ORACLE_SELECT_ONLY
+    for label, lanes, omp in (("single_thread", l1, False), ("all_cores", lall, True)):
+        oracle.use_all_cores(omp)
+        t0 = time.perf_counter()
+        oracle_step(oracle, xadj, adj, w, lanes, spread)
+        dt = time.perf_counter() - t0
+        out[label] = {"value": len(w["ps"]) * 2 * m * lanes / dt / 1e9, "unit": UNIT,
+                      "cores": oracle.threads(), "lanes": lanes, "seconds": dt}
+    oracle.use_all_cores(False)
+    main = out["all_cores"]
+    return {"value": main["value"], "unit": UNIT, "cores": main["cores"], "kind": "oracle",
+            "sample": "one step (%s, K=%d, p in %s) on the first %d of R=%d "
+                      "simulations, OpenMP build on all host cores; single thread on the "
+                      "first %d: %.4g %s" % (oracle_step_kind(name), w["K"], list(w["ps"]),
+                                             lall, w["R"], l1, out["single_thread"]["value"],
+                                             UNIT),
+            "single_thread": out["single_thread"], "all_cores": out["all_cores"],
+            "nproc": os.cpu_count(), "cpu": cpu_model()}
 
 
-def main():
-    args = parse_args()
+def run_ours(args, world):
+    import torch
+
+    import paper_2008_03095_gb300 as im
+    from paper_2008_03095_gb300 import build as lib_build
+    from paper_2008_03095_gb300 import synth
+
+    rank, _, local_rank = dist_env()
+    lib_build.build()
+    im.lib()
+    torch.cuda.set_device(local_rank)
+    w = synth.WORKLOADS[args.workload]
+    xadj, adj = synth.workload_graph(args.workload)
+    rec, results = measure(args.workload, w, xadj, adj, args.steps, args.warmup, world, True)
+    out = {
+        "metric": METRIC, "value": rec.pop("value"), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": rec.pop("ms_per_step"),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic (seeded Chung-Lu / clustered graphs shaped like the paper's "
+                "networks; no dataset)",
+        "config": workload_config(args.workload, xadj, adj, w),
+        "gpu_launches": rec.pop("gpu_launches"),
+    }
+    out.update(rec)
+    out["select_plus_spread_ms_per_query"] = out["ms_per_step"] / len(w["ps"])
+    out["e2e"] = run_e2e(args, xadj, adj, w, world)
+    if not args.no_extra:
+        extra = {}
+        for name in EXTRA_WORKLOADS:
+            if name == args.workload:
+                continue
+            we = synth.WORKLOADS[name]
+            xe, ae = synth.workload_graph(name)
+            r, _ = measure(name, we, xe, ae, args.extra_steps, 2, world, False)
+            r["config"] = workload_config(name, xe, ae, we)
+            r["unit"] = UNIT
+            extra[name] = r
+        out["extra_workloads"] = extra
+    out["paper_context"] = ("no paper number for this graph; the paper's largest comparable "
+                            "runs (Table 4, 2x Xeon E5-2620v4, 16 threads, K=50, p=0.01): "
+                            "Amazon 262k v 2.09 s, NetHEP 15k v 0.08 s, NetPhy 37k v 0.36 s; "
+                            "R not stated")
+    return out, (xadj, adj, w, results)
+
+
+def main(argv=None):
+    args = parse_args(argv)
     rank, world, local_rank = dist_env()
     from paper_2008_03095_gb300 import synth
 
-    w = synth.WORKLOADS[args.workload]
     if args.impl == "reference":
         if rank != 0:
             return 0
+        w = synth.WORKLOADS[args.workload]
         xadj, adj = synth.workload_graph(args.workload)
         print(json.dumps(run_reference(args, xadj, adj, w)))
         return 0
@@ -508,18 +628,12 @@ def main():
         torch.distributed.init_process_group(
             backend="nccl" if torch.cuda.is_available() else "gloo",
             timeout=datetime.timedelta(minutes=10))
-    xadj, adj = synth.workload_graph(args.workload)
-    out = run_ours(args, xadj, adj, w)
-    gpu_results = out.pop("_gpu_results")
-    e2e_fn = out.pop("_e2e")
-    out["e2e"] = e2e_fn()
+    out, (xadj, adj, w, results) = run_ours(args, world)
     if world > 1:
         torch.distributed.barrier()
     if rank == 0:
         if not args.no_cpu_baseline and world == 1:
-            cb, parity = run_cpu_baseline(xadj, adj, w, gpu_results)
-            out["cpu_baseline"] = cb
-            out["parity_vs_oracle"] = parity
+            out["cpu_baseline"] = run_cpu_baseline(args.workload, xadj, adj, w)
         print(json.dumps(out))
     if world > 1:
         torch.distributed.destroy_process_group()
