@@ -73,6 +73,18 @@ def lib():
         L.orc_select_seeds_masked.restype = i32
         L.orc_estimate_spread_masked.argtypes = [i32, i64, P, P, P, i32, i32, P, P]
         L.orc_estimate_spread_masked.restype = i32
+        L.orc_labels_ex.argtypes = [i32, i64, P, P, i32, f64, u32, P, i32, P, P]
+        L.orc_labels_ex.restype = i32
+        L.orc_select_seeds_ex.argtypes = [i32, i64, P, P, i32, i32, f64, u32, P, i32, P, P]
+        L.orc_select_seeds_ex.restype = i32
+        L.orc_estimate_spread_ex.argtypes = [i32, i64, P, P, P, i32, i32, f64, u32, P, i32, P]
+        L.orc_estimate_spread_ex.restype = i32
+        L.orc_live_ex.argtypes = [i32, i32, u32, f64, f64, i32, i32]
+        L.orc_live_ex.restype = i32
+        L.orc_fmix32.argtypes = [u32]
+        L.orc_fmix32.restype = u32
+        L.orc_edge_code.argtypes = [f64]
+        L.orc_edge_code.restype = u32
         L.orc_max_threads.argtypes = []
         L.orc_max_threads.restype = i32
         _libs[_variant] = L
@@ -219,4 +231,61 @@ def estimate_spread_masked(xadj, adj, seeds, mask) -> int:
     out = np.zeros(1, dtype=np.uint64)
     _check(lib().orc_estimate_spread_masked(n, m, _p(xadj), _p(adj), _p(seeds), seeds.shape[0],
                                             R, _p(mask), _p(out)), "estimate_spread_masked")
+    return int(out[0])
+
+
+# ------------------------------------------------------------------ sampling options
+# weights: None for the uniform p, else float64[2m], one probability w(u,v)
+# per CSR arc (equal on both arcs of an edge); mix: the mixed-hash variant.
+
+
+def _w(weights):
+    if weights is None:
+        return None, None
+    w = np.ascontiguousarray(weights, dtype=np.float64)
+    return w, _p(w)
+
+
+def fmix32(h: int) -> int:
+    return int(lib().orc_fmix32(h & 0xFFFFFFFF))
+
+
+def edge_code(w: float) -> int:
+    """32-bit threshold code of an edge probability (0xFFFFFFFF = always live)."""
+    return int(lib().orc_edge_code(w))
+
+
+def live_ex(u, v, x, p=0.0, w=None, mix=False) -> bool:
+    return bool(lib().orc_live_ex(u, v, x & 0xFFFFFFFF, p, 0.0 if w is None else w,
+                                  0 if w is None else 1, 1 if mix else 0))
+
+
+def labels_ex(xadj, adj, R, p, seed, weights=None, mix=False):
+    n, m, xadj, adj = _csr(xadj, adj)
+    w, wp = _w(weights)
+    lab = np.empty((n, R), dtype=np.int32)
+    siz = np.empty((n, R), dtype=np.uint32)
+    _check(lib().orc_labels_ex(n, m, _p(xadj), _p(adj), R, p, seed, wp, 1 if mix else 0,
+                               _p(lab), _p(siz)), "labels_ex")
+    return lab, siz
+
+
+def select_seeds_ex(xadj, adj, K, R, p, seed, weights=None, mix=False):
+    n, m, xadj, adj = _csr(xadj, adj)
+    w, wp = _w(weights)
+    seeds = np.empty(K, dtype=np.int32)
+    sigma = np.empty(K, dtype=np.uint64)
+    _check(lib().orc_select_seeds_ex(n, m, _p(xadj), _p(adj), K, R, p, seed, wp,
+                                     1 if mix else 0, _p(seeds), _p(sigma)), "select_seeds_ex")
+    return seeds, sigma
+
+
+def estimate_spread_ex(xadj, adj, seeds, R, p, seed, weights=None, mix=False) -> int:
+    n, m, xadj, adj = _csr(xadj, adj)
+    w, wp = _w(weights)
+    seeds = np.ascontiguousarray(seeds, dtype=np.int32)
+    out = np.zeros(1, dtype=np.uint64)
+    _check(lib().orc_estimate_spread_ex(n, m, _p(xadj), _p(adj), _p(seeds), seeds.shape[0], R,
+                                        p, seed, wp, 1 if mix else 0, _p(out)),
+           "estimate_spread_ex")
     return int(out[0])

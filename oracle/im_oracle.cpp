@@ -84,6 +84,16 @@ bool csr_ok(int32_t n, int64_t m, const int32_t *xadj, const int32_t *adj) {
 // 4-byte blocks mixed into the state, a 1-3 byte tail, length xor, fmix32.
 uint32_t rotl(uint32_t x, int r) { return (x << r) | (x >> (32 - r)); }
 
+// The avalanche finalizer of MurmurHash3 (fmix32).
+uint32_t fmix32(uint32_t h) {
+  h ^= h >> 16;
+  h *= 0x85ebca6bu;
+  h ^= h >> 13;
+  h *= 0xc2b2ae35u;
+  h ^= h >> 16;
+  return h;
+}
+
 uint32_t murmur3_x86_32(const uint8_t *data, int len, uint32_t seed) {
   const uint32_t c1 = 0xcc9e2d51u, c2 = 0x1b873593u;
   uint32_t h = seed;
@@ -111,12 +121,7 @@ uint32_t murmur3_x86_32(const uint8_t *data, int len, uint32_t seed) {
       h ^= k;
   }
   h ^= (uint32_t)len;
-  h ^= h >> 16;
-  h *= 0x85ebca6bu;
-  h ^= h >> 13;
-  h *= 0xc2b2ae35u;
-  h ^= h >> 16;
-  return h;
+  return fmix32(h);
 }
 
 // Eq. 1: h(u,v) = Murmur3(min(u,v) || max(u,v)).
@@ -144,6 +149,60 @@ struct HashSampler {
     return (uint64_t)(X[r] ^ edge_hash(u, v)) < T;
   }
 };
+
+// Per-edge probabilities w(u,v) (the w_{u,v} of Algorithm 2 and Eq. 2 in place
+// of one uniform p): T_e = floor(w * 2^32) as a 32-bit code c_e; the largest
+// code 2^32 - 1 stands for "always live", so w >= 1 - 2^-32 is certain (the
+// one reading a 32-bit code forces; every other threshold is exact).
+uint32_t edge_code(double w) {
+  const uint64_t T = threshold(w);
+  return T >= 0xffffffffull ? 0xffffffffu : (uint32_t)T;
+}
+
+// Hash sampler with options:
+//   codes  per-arc codes c_a (arc = CSR position) or null for the uniform T
+//   mix    the mixed variant: the XOR of X_r and h goes through fmix32 before
+//          the comparison, so that two edges are co-live with probability
+//          about p^2 whatever their hashes (with the plain XOR, edges whose
+//          hashes differ above T's magnitude are never co-live in a sample)
+struct HashSamplerEx {
+  std::vector<uint32_t> X;
+  uint64_t T;
+  const uint32_t *codes;
+  bool mix;
+  HashSamplerEx(int32_t R, double p, uint32_t seed, const uint32_t *c, bool m)
+      : X(R), T(threshold(p)), codes(c), mix(m) {
+    std::mt19937 gen(seed);
+    for (int32_t r = 0; r < R; ++r) X[r] = (uint32_t)gen();
+  }
+  bool live(int64_t a, int32_t u, int32_t v, int32_t r) const {
+    uint32_t z = X[r] ^ edge_hash(u, v);
+    if (mix) z = fmix32(z);
+    if (codes) return codes[a] == 0xffffffffu || z < codes[a];
+    return (uint64_t)z < T;
+  }
+};
+
+// Weights: one per CSR arc, in [0, 1] (NaN rejected), equal on both arcs of
+// an edge. Fills the per-arc codes.
+bool weights_ok(int32_t n, const int32_t *xadj, const int32_t *adj, const double *w,
+                std::vector<uint32_t> &codes) {
+  const int64_t arcs = xadj[n];
+  codes.resize(arcs);
+  for (int64_t a = 0; a < arcs; ++a) {
+    if (!(w[a] >= 0.0 && w[a] <= 1.0)) return false;
+    codes[a] = edge_code(w[a]);
+  }
+  for (int32_t u = 0; u < n; ++u)
+    for (int32_t a = xadj[u]; a < xadj[u + 1]; ++a) {
+      const int32_t v = adj[a];
+      bool found = false;
+      for (int32_t b = xadj[v]; b < xadj[v + 1]; ++b)
+        if (adj[b] == u && w[b] == w[a]) { found = true; break; }
+      if (!found) return false;
+    }
+  return true;
+}
 
 // Explicit sampler: live[a * R + r] != 0 for arc a (CSR position) in sample r.
 struct MaskSampler {
@@ -387,6 +446,62 @@ int32_t orc_estimate_spread(int32_t n, int64_t m, const int32_t *xadj, const int
   *sigma = spread(n, xadj, adj, R, smp, seeds, ns);
   return 0;
 }
+
+// ----- sampling options: per-arc weights (w: 2m doubles, or null for the
+// uniform p) and the mixed hash (mix != 0)
+int32_t orc_labels_ex(int32_t n, int64_t m, const int32_t *xadj, const int32_t *adj, int32_t R,
+                      double p, uint32_t seed, const double *w, int32_t mix, int32_t *labels,
+                      uint32_t *sizes) {
+  if (!csr_ok(n, m, xadj, adj) || !query_ok(n, R, w ? 0.5 : p)) return -1;
+  std::vector<uint32_t> codes;
+  if (w && !weights_ok(n, xadj, adj, w, codes)) return -1;
+  HashSamplerEx smp(R, w ? 0.0 : p, seed, w ? codes.data() : nullptr, mix != 0);
+  all_labels(n, xadj, adj, R, smp, labels, sizes);
+  return 0;
+}
+
+int32_t orc_select_seeds_ex(int32_t n, int64_t m, const int32_t *xadj, const int32_t *adj,
+                            int32_t K, int32_t R, double p, uint32_t seed, const double *w,
+                            int32_t mix, int32_t *seeds, uint64_t *sigma) {
+  if (!csr_ok(n, m, xadj, adj) || !query_ok(n, R, w ? 0.5 : p) || K < 0 || K > n) return -1;
+  std::vector<uint32_t> codes;
+  if (w && !weights_ok(n, xadj, adj, w, codes)) return -1;
+  HashSamplerEx smp(R, w ? 0.0 : p, seed, w ? codes.data() : nullptr, mix != 0);
+  std::vector<int32_t> labels((size_t)n * R);
+  std::vector<uint32_t> sizes((size_t)n * R);
+  all_labels(n, xadj, adj, R, smp, labels.data(), sizes.data());
+  greedy(n, R, labels.data(), sizes.data(), K, seeds, sigma);
+  return 0;
+}
+
+int32_t orc_estimate_spread_ex(int32_t n, int64_t m, const int32_t *xadj, const int32_t *adj,
+                               const int32_t *seeds, int32_t ns, int32_t R, double p,
+                               uint32_t seed, const double *w, int32_t mix, uint64_t *sigma) {
+  if (!csr_ok(n, m, xadj, adj) || !query_ok(n, R, w ? 0.5 : p) || !seeds_ok(n, seeds, ns))
+    return -1;
+  std::vector<uint32_t> codes;
+  if (w && !weights_ok(n, xadj, adj, w, codes)) return -1;
+  HashSamplerEx smp(R, w ? 0.0 : p, seed, w ? codes.data() : nullptr, mix != 0);
+  *sigma = spread(n, xadj, adj, R, smp, seeds, ns);
+  return 0;
+}
+
+// Live test of one arc under the options: the code of weight w when use_w,
+// else the uniform p; the mixed hash when mix.
+int32_t orc_live_ex(int32_t u, int32_t v, uint32_t x, double p, double w, int32_t use_w,
+                    int32_t mix) {
+  uint32_t z = x ^ edge_hash(u, v);
+  if (mix) z = fmix32(z);
+  if (use_w) {
+    const uint32_t c = edge_code(w);
+    return (c == 0xffffffffu || z < c) ? 1 : 0;
+  }
+  return (uint64_t)z < threshold(p) ? 1 : 0;
+}
+
+uint32_t orc_fmix32(uint32_t h) { return fmix32(h); }
+
+uint32_t orc_edge_code(double w) { return edge_code(w); }
 
 // Greedy from caller-provided label/size tables (n x R, vertex-major).
 int32_t orc_greedy_from_tables(int32_t n, int32_t R, const int32_t *labels, const uint32_t *sizes,

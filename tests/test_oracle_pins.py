@@ -429,3 +429,131 @@ def test_stored_expected_values_match_the_committed_graph_digests():
         assert (K, R, seed) == (w["K"], w["R"], w["rng_seed"]) and p in w["ps"]
         assert len(set(seeds.tolist())) == K and len(sigma) == K
         assert sigma[0] > 0 and np.all(np.diff(sigma.astype(np.int64)) >= 0)
+
+
+# ------------------------------------------------------------------ per-edge weights, mixed hash
+
+
+def test_fmix32_is_murmur3_of_the_empty_key():
+    """MurmurHash3 of an empty key is the finalizer applied to the seed, so the
+    published empty-key vectors pin fmix32 (and fmix32 is a bijection)."""
+    for key_hex, seed_hex, exp_hex in _util.golden_lines("murmur3_x86_32_vectors.txt"):
+        if key_hex == "-":
+            assert oracle.fmix32(int(seed_hex, 16)) == int(exp_hex, 16)
+    xs = np.random.default_rng(3).integers(0, 2 ** 32, size=20000, dtype=np.uint64)
+    assert len({oracle.fmix32(int(x)) for x in xs}) == len(set(xs.tolist()))
+
+
+def test_edge_codes_closed_forms():
+    assert oracle.edge_code(0.0) == 0
+    assert oracle.edge_code(1.0) == 0xFFFFFFFF
+    assert oracle.edge_code(0.5) == 2 ** 31
+    assert oracle.edge_code(2.0 ** -32) == 1
+    for p in (0.01, 0.05, 0.3, 0.999):
+        assert oracle.edge_code(p) == oracle.threshold(p)
+    u, v = 3, 9
+    for x in (0, 1, 12345, 2 ** 32 - 1):
+        assert not oracle.live_ex(u, v, x, w=0.0)
+        assert oracle.live_ex(u, v, x, w=1.0)
+        assert oracle.live_ex(u, v, x, p=0.01, w=0.01) == oracle.live(u, v, x, 0.01)
+        assert not oracle.live_ex(u, v, x, p=0.0, mix=True)
+        assert oracle.live_ex(u, v, x, p=1.0, mix=True)
+        z = x ^ oracle.edge_hash(u, v)
+        assert oracle.live_ex(u, v, x, p=0.3, mix=True) == (oracle.fmix32(z) < oracle.threshold(0.3))
+
+
+def _arc_weights(xadj, adj, fn):
+    n = xadj.shape[0] - 1
+    src = np.repeat(np.arange(n), np.diff(xadj))
+    lo, hi = np.minimum(src, adj), np.maximum(src, adj)
+    return fn(lo, hi)
+
+
+def test_uniform_weights_equal_uniform_p():
+    xadj, adj = synth.chung_lu(800, 3200, 2.3, 31)
+    for p in (0.01, 0.1, 0.5):
+        w = _arc_weights(xadj, adj, lambda lo, hi: np.full(lo.shape, p))
+        a = oracle.select_seeds(xadj, adj, 12, 64, p, 5)
+        b = oracle.select_seeds_ex(xadj, adj, 12, 64, 0.0, 5, weights=w)
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+        assert np.array_equal(oracle.labels(xadj, adj, 64, p, 5)[0],
+                              oracle.labels_ex(xadj, adj, 64, 0.9, 5, weights=w)[0])
+
+
+def test_zero_one_weights_give_the_components_of_the_certain_edges():
+    xadj, adj = synth.random_graph(300, 700, 32)
+    n = 300
+    keep = lambda lo, hi: ((lo * 7 + hi * 13) % 3 == 0)  # noqa: E731
+    w = _arc_weights(xadj, adj, lambda lo, hi: keep(lo, hi).astype(np.float64))
+    src = np.repeat(np.arange(n), np.diff(xadj))
+    sel = keep(np.minimum(src, adj), np.maximum(src, adj))
+    A = coo_matrix((np.ones(int(sel.sum())), (src[sel], adj[sel])), shape=(n, n))
+    _, comp = connected_components(A, directed=False)
+    minid = np.full(comp.max() + 1, n)
+    np.minimum.at(minid, comp, np.arange(n))
+    lab, siz = oracle.labels_ex(xadj, adj, 16, 0.0, 9, weights=w)
+    for r in range(16):
+        assert np.array_equal(lab[:, r], minid[comp])
+    for mix in (False, True):
+        assert np.array_equal(oracle.labels_ex(xadj, adj, 4, 0.0, 9, weights=w, mix=mix)[0][:, 0],
+                              minid[comp])
+
+
+def test_weighted_and_mixed_live_rates_within_five_standard_errors():
+    rng = np.random.default_rng(11)
+    X = oracle.mt19937(1234, 40000)
+    for (u, v, w, mix) in ((1, 2, 0.3, False), (5, 77, 0.05, False), (8, 9, 0.05, True),
+                           (10, 400, 0.3, True)):
+        hits = sum(oracle.live_ex(u, v, int(x), p=w, mix=mix) if mix else
+                   oracle.live_ex(u, v, int(x), w=w) for x in X)
+        q = oracle.edge_code(w) / 2.0 ** 32
+        se = math.sqrt(q * (1 - q) / len(X))
+        assert abs(hits / len(X) - q) < 5 * se, (u, v, w, mix)
+    del rng
+
+
+def test_mixed_hash_decorrelates_edges_the_plain_xor_never_samples_together():
+    """With the plain XOR at p = 2^-6, an edge is live only when the top six
+    bits of X_r equal those of its hash, so two edges whose hashes differ there
+    are never live in the same sample; through fmix32 they are co-live at a
+    rate near p^2."""
+    p = 2.0 ** -6
+    pairs = []
+    for u in range(1, 200):
+        h1, h2 = oracle.edge_hash(0, u), oracle.edge_hash(0, u + 1000)
+        if (h1 >> 26) != (h2 >> 26):
+            pairs.append((u, u + 1000))
+        if len(pairs) == 3:
+            break
+    X = oracle.mt19937(99, 60000)
+    for u, v in pairs:
+        plain = sum(oracle.live(0, u, int(x), p) and oracle.live(0, v, int(x), p) for x in X)
+        assert plain == 0
+        mixed = sum(oracle.live_ex(0, u, int(x), p=p, mix=True)
+                    and oracle.live_ex(0, v, int(x), p=p, mix=True) for x in X)
+        se = math.sqrt(p * p * (1 - p * p) / len(X))
+        assert abs(mixed / len(X) - p * p) < 5 * se
+
+
+def test_options_greedy_agrees_with_its_tables_and_bfs_spread():
+    xadj, adj = synth.chung_lu(600, 3000, 2.2, 33)
+    w = _arc_weights(xadj, adj, lambda lo, hi: ((lo * 31 + hi * 17) % 100) / 1000.0)  # U-like [0, 0.1)
+    for kw in (dict(weights=w), dict(mix=True), dict(weights=w, mix=True)):
+        lab, siz = oracle.labels_ex(xadj, adj, 48, 0.05, 3, **kw)
+        s, g = oracle.select_seeds_ex(xadj, adj, 10, 48, 0.05, 3, **kw)
+        s2, g2 = oracle.greedy_from_tables(lab, siz, 10)
+        assert np.array_equal(s, s2) and np.array_equal(g, g2)
+        for k in (0, 4, 9):
+            assert oracle.estimate_spread_ex(xadj, adj, s[:k + 1], 48, 0.05, 3, **kw) == int(g[k])
+
+
+def test_weights_must_be_symmetric_and_in_range():
+    xadj, adj = synth.random_graph(50, 100, 34)
+    w = np.full(adj.shape[0], 0.2)
+    w[0] = 0.3  # one arc differs from its reverse
+    with pytest.raises(ValueError):
+        oracle.select_seeds_ex(xadj, adj, 3, 8, 0.0, 1, weights=w)
+    for bad in (-0.1, 1.5, np.nan):
+        w = np.full(adj.shape[0], bad)
+        with pytest.raises(ValueError):
+            oracle.labels_ex(xadj, adj, 8, 0.0, 1, weights=w)
