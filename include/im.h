@@ -72,6 +72,20 @@ typedef struct im_workspace im_workspace; /* opaque, library-owned */
 int im_graph_create(int32_t n, int64_t m, const int32_t *xadj, const int32_t *adj,
                     im_graph **out);
 
+/* Same as im_graph_create, with a probability per edge instead of one uniform
+ * p (the w_{u,v} of Algorithm 2 and Eq. 2, Section 4's weight settings):
+ * w[2m] is a host array with one value per CSR arc, in [0, 1] (NaN
+ * rejected), and both orientations of an edge carry the same value (for
+ * duplicate arcs: the same multiset of values). Each weight becomes the
+ * threshold code c = floor(w * 2^32) of Eq. 2, where the largest 32-bit code
+ * means "always live" (so w >= 1 - 2^-32 is certain); the codes stay on the
+ * device with the graph (4 bytes per arc and per edge). Queries use them
+ * when called with IM_SAMPLE_EDGE_WEIGHTS; plain queries still take p.
+ * Errors: as im_graph_create, and IM_EINVAL for out-of-range or asymmetric
+ * weights. */
+int im_graph_create_weighted(int32_t n, int64_t m, const int32_t *xadj, const int32_t *adj,
+                             const double *w, im_graph **out);
+
 /* Release a graph and its device memory (and its internal workspace). */
 int im_graph_destroy(im_graph *g);
 
@@ -93,6 +107,38 @@ int im_select_seeds(const im_graph *g, int32_t K, int32_t R, double p, uint32_t 
  * host array of num_seeds ids; duplicates count once. Blocking. */
 int im_estimate_spread(const im_graph *g, const int32_t *seeds, int32_t num_seeds, int32_t R,
                        double p, uint32_t rng_seed, uint64_t *out_sigma_R);
+
+/* Options of the _ex queries (bit flags):
+ *   IM_SAMPLE_EDGE_WEIGHTS  sample edge {u,v} with the graph's own w(u,v)
+ *                           (im_graph_create_weighted); p is ignored
+ *   IM_SAMPLE_MIXED_HASH    live iff fmix32(X_r XOR h(u,v)) < T, fmix32 being
+ *                           MurmurHash3's finalizer: with the plain XOR of
+ *                           Eq. 2, edges whose hashes differ above T's
+ *                           magnitude are never live in the same sample; the
+ *                           mix makes co-sampling rates match independent
+ *                           edges (a variant of this library, not the paper's
+ *                           scheme; every lane is then tested for every edge)
+ *   IM_ALGO_FUSED_SAMPLING  select only: the FusedSampling variant the paper
+ *                           measures in Section 4 (Table 4): the same fused
+ *                           hash sampling, but one simulation at a time and no
+ *                           memoized labels -- the NewGreedy step runs R
+ *                           single-simulation component passes, and every CELF
+ *                           re-evaluation recomputes the spread of S + {u}
+ *                           over the R samples one by one (Algorithm 3's
+ *                           RandCas on the fixed samples). Same seeds and
+ *                           sigma*R as the default path; a baseline of cost.
+ * The options combine, except that IM_ALGO_FUSED_SAMPLING is blocking only. */
+enum {
+  IM_SAMPLE_EDGE_WEIGHTS = 1,
+  IM_SAMPLE_MIXED_HASH = 2,
+  IM_ALGO_FUSED_SAMPLING = 4
+};
+
+/* im_select_seeds / im_estimate_spread with options (flags above). */
+int im_select_seeds_ex(const im_graph *g, int32_t K, int32_t R, double p, uint32_t rng_seed,
+                       uint32_t flags, int32_t *out_seeds, uint64_t *out_sigma_R);
+int im_estimate_spread_ex(const im_graph *g, const int32_t *seeds, int32_t num_seeds, int32_t R,
+                          double p, uint32_t rng_seed, uint32_t flags, uint64_t *out_sigma_R);
 
 /* Limits of im_estimate_spread_noalloc (the size of its static scratch). */
 #define IM_NOALLOC_MAX_N 32768      /* vertices; also the largest num_seeds */
@@ -140,6 +186,14 @@ int im_select_seeds_async(const im_graph *g, im_workspace *ws, int32_t K, int32_
 int im_estimate_spread_async(const im_graph *g, im_workspace *ws, const int32_t *d_seeds,
                              int32_t num_seeds, int32_t R, double p, uint32_t rng_seed,
                              uint64_t *d_sigma_R);
+
+/* The async queries with options (IM_SAMPLE_* flags only). */
+int im_select_seeds_ex_async(const im_graph *g, im_workspace *ws, int32_t K, int32_t R, double p,
+                             uint32_t rng_seed, uint32_t flags, int32_t *d_seeds,
+                             uint64_t *d_sigma_R);
+int im_estimate_spread_ex_async(const im_graph *g, im_workspace *ws, const int32_t *d_seeds,
+                                int32_t num_seeds, int32_t R, double p, uint32_t rng_seed,
+                                uint32_t flags, uint64_t *d_sigma_R);
 
 /* Synchronize the thread's stream and return (then clear) the first device
  * status recorded in ws since the last call: IM_OK, IM_EINVAL, IM_ETIMEOUT or
@@ -230,6 +284,11 @@ int im_debug_tables_lanes(const im_graph *g, int32_t R, double p, uint32_t rng_s
                           const int32_t *lanes, int32_t num_lanes, int32_t *out_labels,
                           uint32_t *out_sizes);
 
+/* Labels and sizes (layouts of im_debug_labels / im_debug_sizes) under the
+ * sampling options (IM_SAMPLE_* flags); either output may be NULL. */
+int im_debug_tables_ex(const im_graph *g, int32_t R, double p, uint32_t rng_seed, uint32_t flags,
+                       int32_t *out_labels, uint32_t *out_sizes);
+
 /* First-seed marginal gains of the NewGreedy step (Algorithm 5, final loop):
  * out_mg[v] = sum_r |C_r(v)|, the n values the lazy greedy starts from, as
  * the device computed them (host array of n uint64 values). */
@@ -270,7 +329,9 @@ enum {
   IM_OVR_SPREAD_LEVEL_CAP = 3, /* budget of spread BFS levels (exceeded: IM_ETIMEOUT) */
   IM_OVR_FAIL_ALLOC = 4,       /* the value-th device allocation from now fails as if the
                                   device were out of memory (1 = the next one); one shot */
-  IM_NUM_OVERRIDES = 5
+  IM_OVR_CELF_REFRESH_AFTER = 5, /* lazy greedy: exact evaluations without a commit before all
+                                    gains are recomputed (any value keeps the result exact) */
+  IM_NUM_OVERRIDES = 6
 };
 /* Errors: IM_EINVAL (unknown key, or a value outside the key's range). */
 int im_debug_override(int32_t key, int64_t value);

@@ -74,6 +74,12 @@ def lib():
         "im_debug_select_seeds_masked": [P, i32, i32, P, P, P, P, P],
         "im_debug_estimate_spread_masked": [P, P, i32, i32, P, P],
         "im_debug_override": [i32, i64],
+        "im_graph_create_weighted": [i32, i64, P, P, P, P],
+        "im_debug_tables_ex": [P, i32, f64, u32, u32, P, P],
+        "im_select_seeds_ex": [P, i32, i32, f64, u32, u32, P, P],
+        "im_estimate_spread_ex": [P, P, i32, i32, f64, u32, u32, P],
+        "im_select_seeds_ex_async": [P, P, i32, i32, f64, u32, u32, P, P],
+        "im_estimate_spread_ex_async": [P, P, P, i32, i32, f64, u32, u32, P],
         "im_debug_first_gains": [P, i32, f64, u32, P],
         "im_profile_enable": [ctypes.c_int],
         "im_profile_read": [P, P],
@@ -171,6 +177,52 @@ def im_graph_create(xadj, adj):
     _check(lib().im_graph_create(n, m, _ptr(xadj), _ptr(adj) if adj.size else None,
                                  ctypes.byref(out)))
     return Graph(out, n, m)
+
+
+IM_SAMPLE_EDGE_WEIGHTS = 1
+IM_SAMPLE_MIXED_HASH = 2
+IM_ALGO_FUSED_SAMPLING = 4
+
+
+def im_graph_create_weighted(xadj, adj, w):
+    """Graph with one probability per CSR arc (float64[2m])."""
+    xadj = np.ascontiguousarray(xadj, dtype=np.int32)
+    adj = np.ascontiguousarray(adj, dtype=np.int32)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    n = xadj.shape[0] - 1
+    m = adj.shape[0] // 2
+    if w.shape[0] != adj.shape[0]:
+        raise ValueError("one weight per CSR arc is required")
+    out = ctypes.c_void_p()
+    _check(lib().im_graph_create_weighted(n, m, _ptr(xadj), _ptr(adj) if adj.size else None,
+                                          _ptr(w) if w.size else None, ctypes.byref(out)))
+    return Graph(out, n, m)
+
+
+def im_select_seeds_ex(g, K, R, p, rng_seed, flags, out_seeds=None, out_sigma=None):
+    seeds = np.empty(max(K, 0), dtype=np.int32) if out_seeds is None else out_seeds
+    sigma = np.empty(max(K, 0), dtype=np.uint64) if out_sigma is None else out_sigma
+    _check(lib().im_select_seeds_ex(_gh(g), K, R, p, rng_seed & 0xFFFFFFFF, flags, _ptr(seeds),
+                                    _ptr(sigma)))
+    return seeds, sigma
+
+
+def im_estimate_spread_ex(g, seeds, R, p, rng_seed, flags):
+    seeds = np.ascontiguousarray(seeds, dtype=np.int32)
+    out = ctypes.c_uint64()
+    _check(lib().im_estimate_spread_ex(_gh(g), _ptr(seeds), seeds.shape[0], R, p,
+                                       rng_seed & 0xFFFFFFFF, flags, ctypes.byref(out)))
+    return int(out.value)
+
+
+def im_select_seeds_ex_async(g, ws, K, R, p, rng_seed, flags, d_seeds, d_sigma):
+    _check(lib().im_select_seeds_ex_async(_gh(g), ws.handle, K, R, p, rng_seed & 0xFFFFFFFF,
+                                          flags, _ptr(d_seeds), _ptr(d_sigma)))
+
+
+def im_estimate_spread_ex_async(g, ws, d_seeds, num_seeds, R, p, rng_seed, flags, d_sigma):
+    _check(lib().im_estimate_spread_ex_async(_gh(g), ws.handle, _ptr(d_seeds), num_seeds, R, p,
+                                             rng_seed & 0xFFFFFFFF, flags, _ptr(d_sigma)))
 
 
 def im_graph_create_raw(n, m, xadj_ptr, adj_ptr):
@@ -322,6 +374,15 @@ def im_debug_first_gains(g, R, p, rng_seed):
     return out
 
 
+def im_debug_tables_ex(g, R, p, rng_seed, flags):
+    """(labels int32[n, R], sizes uint32[n, R]) under the IM_SAMPLE_* options."""
+    lab = np.empty((g.n, R), dtype=np.int32)
+    siz = np.empty((g.n, R), dtype=np.uint32)
+    _check(lib().im_debug_tables_ex(_gh(g), R, p, rng_seed & 0xFFFFFFFF, flags, _ptr(lab),
+                                    _ptr(siz)))
+    return lab, siz
+
+
 def im_debug_sizes(g, R, p, rng_seed):
     out = np.empty((g.n, R), dtype=np.uint32)
     _check(lib().im_debug_sizes(_gh(g), R, p, rng_seed & 0xFFFFFFFF, _ptr(out)))
@@ -359,7 +420,8 @@ IM_OVR_CELF_ROUND_CAP = 1
 IM_OVR_UF_CAP = 2
 IM_OVR_SPREAD_LEVEL_CAP = 3
 IM_OVR_FAIL_ALLOC = 4
-IM_NUM_OVERRIDES = 5
+IM_OVR_CELF_REFRESH_AFTER = 5
+IM_NUM_OVERRIDES = 6
 
 
 def im_debug_override(key, value):

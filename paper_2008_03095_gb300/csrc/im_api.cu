@@ -7,6 +7,9 @@
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <queue>
+#include <algorithm>
+#include <utility>
 #include <string>
 #include <vector>
 
@@ -194,6 +197,37 @@ int make_params(const im_graph *g, int32_t R, double p, uint32_t seed, QueryPara
     if (nb > kMaxBucketBits) nb = kMaxBucketBits;
   }
   q->nb = nb;
+  q->weighted = 0;
+  q->mix = 0;
+  return IM_OK;
+}
+
+constexpr uint32_t kSampleFlags = IM_SAMPLE_EDGE_WEIGHTS | IM_SAMPLE_MIXED_HASH;
+
+// Parameters under the sampling options (flags: IM_SAMPLE_*). Weighted
+// queries ignore p; their lanes are sorted by the top kMaxBucketBits bits of X
+// so that every edge code finds its candidate lanes as one run (edge_lanes).
+// The mixed hash cannot be bucketed: every lane is a candidate.
+int make_params_ex(const im_graph *g, int32_t R, double p, uint32_t seed, uint32_t flags,
+                   QueryParams *q) {
+  if (flags & ~kSampleFlags) return fail(IM_EINVAL, "unknown sampling flags 0x%x", flags);
+  const bool weighted = (flags & IM_SAMPLE_EDGE_WEIGHTS) != 0;
+  if (weighted && !(g && g->d_code_arc))
+    return fail(IM_EINVAL, "IM_SAMPLE_EDGE_WEIGHTS on a graph created without edge weights");
+  int rc = make_params(g, R, weighted ? 0.5 : p, seed, q);
+  if (rc != IM_OK) return rc;
+  if (weighted) {
+    q->weighted = 1;
+    q->T = 0;
+    q->T32 = 0;
+    q->all_live = 0;
+    q->none_live = 0;
+    q->nb = kMaxBucketBits;
+  }
+  if (flags & IM_SAMPLE_MIXED_HASH) {
+    q->mix = 1;
+    q->nb = 0;
+  }
   return IM_OK;
 }
 
@@ -368,6 +402,144 @@ int ensure_seed_in(im_workspace *ws, int64_t count) {
   return IM_OK;
 }
 
+// FusedSampling (Section 4, Table 4): MixGreedy with the paper's fused hash
+// sampling but none of its batching or memoization. Simulation r runs alone
+// on a one-lane view of the workspace (its X_r, one lane bucket): the
+// NewGreedy step hooks and compresses a single-lane label array per
+// simulation and adds the component sizes into mg; the lazy greedy keeps a
+// host priority queue ordered by (gain descending, id ascending) with
+// MixGreedy's iteration stamps, and re-evaluates a stale top u by RandCas on
+// the fixed samples: the spread of S + {u}, one single-lane BFS launch per
+// simulation, minus sigma(S). Gains are exact integers, so the committed
+// sequence is the naive greedy one (the same seeds and sigma*R as the default
+// path).
+int fused_sampling_select(im_graph *g, im_workspace *ws, int32_t K, const QueryParams &q,
+                          int32_t *out_seeds, uint64_t *out_sigma, cudaStream_t s) {
+  const uint32_t R = q.R;
+  const size_t n = (size_t)g->n;
+  // the lane randoms X_0..X_{R-1} in simulation order (ws->d_X)
+  QueryParams qa = q;
+  qa.nb = 0;
+  API_CUDA(timed(IM_PHASE_PREP, s, [&] { return launch_prep(ws, qa, false, false, s); }),
+           "k_prep");
+  unsigned long long *d_mg = nullptr, *d_acc = nullptr;
+  uint32_t *d_boff1 = nullptr;
+  cudaError_t e = dev_malloc(reinterpret_cast<void **>(&d_mg), sizeof(unsigned long long) * n);
+  if (e == cudaSuccess) e = dev_malloc(reinterpret_cast<void **>(&d_acc), sizeof(uint64_t) * R);
+  if (e == cudaSuccess) e = dev_malloc(reinterpret_cast<void **>(&d_boff1), 2 * sizeof(uint32_t));
+  const uint32_t boff1[2] = {0u, 1u};  // one lane, one bucket
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_mg, 0, sizeof(unsigned long long) * n, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d_boff1, boff1, sizeof(boff1), cudaMemcpyHostToDevice, s);
+  auto release = [&] {
+    if (d_mg) cudaFree(d_mg);
+    if (d_acc) cudaFree(d_acc);
+    if (d_boff1) cudaFree(d_boff1);
+  };
+  if (e != cudaSuccess) {
+    release();
+    return cuda_fail(e, "FusedSampling buffers");
+  }
+  int rc = ensure_seed_in(ws, K + 1);
+  if (rc != IM_OK) {
+    release();
+    return rc;
+  }
+  QueryParams q1 = q;  // one simulation: R = 1, one bucket
+  q1.R = 1;
+  q1.nb = 0;
+  im_workspace v1 = *ws;  // one-lane view sharing the workspace's buffers
+  v1.d_boff = d_boff1;
+  v1.d_X = nullptr;
+  v1.d_perm = nullptr;
+  v1.d_sortbuf = nullptr;
+  v1.d_keyrange = nullptr;
+  int32_t *P1 = ws->d_P;  // the first n slots of the label table
+  // ---- NewGreedy step, one simulation at a time
+  for (uint32_t r = 0; r < R && e == cudaSuccess; ++r) {
+    v1.d_Xs = ws->d_X + r;
+    e = timed(IM_PHASE_PREP, s, [&] { return launch_fs_init(g, P1, s); });
+    if (e == cudaSuccess && !q1.none_live && g->m_up > 0) {
+      e = timed(IM_PHASE_UNION, s, [&] { return launch_union(g, &v1, q1, nullptr, s); });
+      if (e == cudaSuccess)
+        e = timed(IM_PHASE_COMPRESS, s, [&] { return launch_compress(g, &v1, q1, s); });
+    }
+    if (e == cudaSuccess)
+      e = timed(IM_PHASE_GAINS, s, [&] { return launch_fs_accum(g, P1, d_mg, s); });
+  }
+  std::vector<unsigned long long> mg(n);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(mg.data(), d_mg, sizeof(unsigned long long) * n, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    release();
+    return cuda_fail(e, "FusedSampling NewGreedy step");
+  }
+  rc = take_status(ws, s);
+  if (rc != IM_OK) {
+    release();
+    return rc;
+  }
+  // ---- lazy greedy (CELF) with RandCas re-evaluations
+  using Entry = std::pair<uint64_t, int64_t>;  // (gain, -id): the max is the largest gain, lowest id
+  std::priority_queue<Entry> pq;
+  std::vector<uint64_t> gain(n);
+  std::vector<int32_t> iter(n, 0);
+  std::vector<uint8_t> chosen(n, 0);
+  for (size_t v = 0; v < n; ++v) {
+    gain[v] = mg[v];
+    pq.push(Entry(mg[v], -(int64_t)v));
+  }
+  std::vector<int32_t> S;
+  std::vector<uint64_t> acc(R);
+  uint64_t sigma = 0;
+  while ((int32_t)S.size() < K && !pq.empty()) {
+    const Entry top = pq.top();
+    pq.pop();
+    const int32_t u = (int32_t)(-top.second);
+    if (chosen[u] || top.first != gain[u]) continue;  // a superseded entry
+    if (iter[u] == (int32_t)S.size()) {
+      chosen[u] = 1;
+      S.push_back(u);
+      sigma += gain[u];
+      out_seeds[S.size() - 1] = u;
+      out_sigma[S.size() - 1] = sigma;
+      continue;
+    }
+    // RandCas(S + {u}) over the R fixed samples, one simulation per launch
+    std::vector<int32_t> Su(S);
+    Su.push_back(u);
+    e = cudaMemcpyAsync(ws->d_seeds_in, Su.data(), sizeof(int32_t) * Su.size(),
+                        cudaMemcpyHostToDevice, s);
+    for (uint32_t r = 0; r < R && e == cudaSuccess; ++r) {
+      v1.d_Xs = ws->d_X + r;
+      e = timed(IM_PHASE_SPREAD, s, [&] {
+        return launch_spread(g, &v1, q1, ws->d_seeds_in, (int)Su.size(), nullptr,
+                             reinterpret_cast<uint64_t *>(d_acc) + r, s);
+      });
+    }
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(acc.data(), d_acc, sizeof(uint64_t) * R, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+      release();
+      return cuda_fail(e, "FusedSampling RandCas");
+    }
+    uint64_t tot = 0;
+    for (uint32_t r = 0; r < R; ++r) tot += acc[r];
+    if (tot < sigma) {
+      release();
+      return fail(IM_EINTERNAL, "spread of S + {u} below spread of S");
+    }
+    gain[u] = tot - sigma;
+    iter[u] = (int32_t)S.size();
+    pq.push(Entry(gain[u], -(int64_t)u));
+  }
+  release();
+  if ((int32_t)S.size() < K) return fail(IM_EINTERNAL, "priority queue ran dry");
+  return take_status(ws, s);
+}
+
 }  // namespace
 
 namespace {
@@ -494,8 +666,44 @@ int im_sampling_threshold(double p, uint64_t *out_T) {
   return IM_OK;
 }
 
+// Per-arc probabilities: each in [0, 1], and both orientations of an edge
+// carry the same multiset of values (duplicate arcs may differ among
+// themselves). Self-loops are ignored like their arcs.
+static int check_weights(int32_t n, const int32_t *xadj, const int32_t *adj, const double *w) {
+  const int64_t arcs = xadj[n];
+  std::vector<std::pair<uint64_t, double>> fwd, bwd;
+  for (int32_t u = 0; u < n; ++u)
+    for (int32_t a = xadj[u]; a < xadj[u + 1]; ++a) {
+      if (!(w[a] >= 0.0 && w[a] <= 1.0))
+        return fail(IM_EINVAL, "edge weight of arc %lld outside [0, 1] or NaN", (long long)a);
+      const int32_t v = adj[a];
+      if (v < 0 || v >= n || v == u) continue;
+      const uint64_t key = ((uint64_t)(uint32_t)(u < v ? u : v) << 32) | (uint32_t)(u < v ? v : u);
+      (u < v ? fwd : bwd).emplace_back(key, w[a]);
+    }
+  (void)arcs;
+  std::sort(fwd.begin(), fwd.end());
+  std::sort(bwd.begin(), bwd.end());
+  if (fwd != bwd) return fail(IM_EINVAL, "edge weights differ between the two arcs of an edge");
+  return IM_OK;
+}
+
+static int graph_create_impl(int32_t n, int64_t m, const int32_t *xadj, const int32_t *adj,
+                             const double *w, im_graph **out);
+
 int im_graph_create(int32_t n, int64_t m, const int32_t *xadj, const int32_t *adj,
                     im_graph **out) {
+  return graph_create_impl(n, m, xadj, adj, nullptr, out);
+}
+
+int im_graph_create_weighted(int32_t n, int64_t m, const int32_t *xadj, const int32_t *adj,
+                             const double *w, im_graph **out) {
+  if (m > 0 && !w) return fail(IM_EINVAL, "null weights");
+  return graph_create_impl(n, m, xadj, adj, w ? w : nullptr, out);
+}
+
+static int graph_create_impl(int32_t n, int64_t m, const int32_t *xadj, const int32_t *adj,
+                             const double *w, im_graph **out) {
   if (!out) return fail(IM_EINVAL, "null output handle");
   if (n < 1) return fail(IM_EINVAL, "n=%d must be >= 1", n);
   if (m < 0) return fail(IM_EINVAL, "m must be >= 0");
@@ -515,12 +723,28 @@ int im_graph_create(int32_t n, int64_t m, const int32_t *xadj, const int32_t *ad
     return cuda_fail(e, "device query");
   }
   char err[256] = {0};
-  int rc = graph_build_device(g, xadj, adj, err, sizeof(err));
+  const bool weighted = w != nullptr;
+  if (weighted) {
+    // the CSR shape is checked before the weights are indexed by it
+    for (int32_t u = 0; u < n; ++u)
+      if (xadj[u + 1] < xadj[u] || xadj[u] < 0 || (int64_t)xadj[u + 1] > 2 * m) {
+        delete g;
+        return fail(IM_EINVAL, "xadj is not non-decreasing within [0, 2m]");
+      }
+    const int wrc = check_weights(n, xadj, adj, w);
+    if (wrc != IM_OK) {
+      delete g;
+      return wrc;
+    }
+  }
+  int rc = graph_build_device(g, xadj, adj, w, err, sizeof(err));
   if (rc != IM_OK) {
     if (g->d_xadj) cudaFree(g->d_xadj);
     if (g->d_adj) cudaFree(g->d_adj);
     if (g->d_eu) cudaFree(g->d_eu);
     if (g->d_ev) cudaFree(g->d_ev);
+    if (g->d_code_arc) cudaFree(g->d_code_arc);
+    if (g->d_code_up) cudaFree(g->d_code_up);
     delete g;
     return fail(rc, "%s", err);
   }
@@ -539,6 +763,8 @@ int im_graph_destroy(im_graph *g) {
   if (g->d_adj) cudaFree(g->d_adj);
   if (g->d_eu) cudaFree(g->d_eu);
   if (g->d_ev) cudaFree(g->d_ev);
+  if (g->d_code_arc) cudaFree(g->d_code_arc);
+  if (g->d_code_up) cudaFree(g->d_code_up);
   delete g;
   return IM_OK;
 }
@@ -586,42 +812,56 @@ int im_workspace_stats(im_workspace *ws, int64_t *out) {
   return IM_OK;
 }
 
-int im_select_seeds_async(const im_graph *g, im_workspace *ws, int32_t K, int32_t R, double p,
-                          uint32_t rng_seed, int32_t *d_seeds, uint64_t *d_sigma_R) {
+int im_select_seeds_ex_async(const im_graph *g, im_workspace *ws, int32_t K, int32_t R, double p,
+                             uint32_t rng_seed, uint32_t flags, int32_t *d_seeds,
+                             uint64_t *d_sigma_R) {
   int rc = check_ws(g, ws, R);
   if (rc != IM_OK) return rc;
   if (K < 0 || K > g->n) return fail(IM_EINVAL, "K=%d outside [0, n=%d]", K, g->n);
   if (K > 0 && (!d_seeds || !d_sigma_R)) return fail(IM_EINVAL, "null output");
+  if (flags & IM_ALGO_FUSED_SAMPLING)
+    return fail(IM_EINVAL, "IM_ALGO_FUSED_SAMPLING is blocking only (im_select_seeds_ex)");
   QueryParams q;
-  rc = make_params(g, R, p, rng_seed, &q);
+  rc = make_params_ex(g, R, p, rng_seed, flags, &q);
   if (rc != IM_OK) return rc;
   if (K == 0) return IM_OK;
   DeviceGuard dg(g->device);
   return enqueue_select(g, ws, K, q, nullptr, d_seeds, d_sigma_R, t_stream, false);
 }
 
-int im_estimate_spread_async(const im_graph *g, im_workspace *ws, const int32_t *d_seeds,
-                             int32_t num_seeds, int32_t R, double p, uint32_t rng_seed,
-                             uint64_t *d_sigma_R) {
+int im_select_seeds_async(const im_graph *g, im_workspace *ws, int32_t K, int32_t R, double p,
+                          uint32_t rng_seed, int32_t *d_seeds, uint64_t *d_sigma_R) {
+  return im_select_seeds_ex_async(g, ws, K, R, p, rng_seed, 0u, d_seeds, d_sigma_R);
+}
+
+int im_estimate_spread_ex_async(const im_graph *g, im_workspace *ws, const int32_t *d_seeds,
+                                int32_t num_seeds, int32_t R, double p, uint32_t rng_seed,
+                                uint32_t flags, uint64_t *d_sigma_R) {
   int rc = check_ws(g, ws, R);
   if (rc != IM_OK) return rc;
   if (num_seeds < 0) return fail(IM_EINVAL, "num_seeds < 0");
   if (!d_sigma_R || (num_seeds > 0 && !d_seeds)) return fail(IM_EINVAL, "null argument");
   QueryParams q;
-  rc = make_params(g, R, p, rng_seed, &q);
+  rc = make_params_ex(g, R, p, rng_seed, flags, &q);
   if (rc != IM_OK) return rc;
   DeviceGuard dg(g->device);
   return enqueue_spread(g, ws, d_seeds, num_seeds, q, nullptr, d_sigma_R, t_stream);
 }
 
-int im_select_seeds(const im_graph *g_, int32_t K, int32_t R, double p, uint32_t rng_seed,
-                    int32_t *out_seeds, uint64_t *out_sigma_R) {
+int im_estimate_spread_async(const im_graph *g, im_workspace *ws, const int32_t *d_seeds,
+                             int32_t num_seeds, int32_t R, double p, uint32_t rng_seed,
+                             uint64_t *d_sigma_R) {
+  return im_estimate_spread_ex_async(g, ws, d_seeds, num_seeds, R, p, rng_seed, 0u, d_sigma_R);
+}
+
+int im_select_seeds_ex(const im_graph *g_, int32_t K, int32_t R, double p, uint32_t rng_seed,
+                       uint32_t flags, int32_t *out_seeds, uint64_t *out_sigma_R) {
   if (!g_) return fail(IM_EINVAL, "null graph");
   im_graph *g = const_cast<im_graph *>(g_);
   if (K < 0 || K > g->n) return fail(IM_EINVAL, "K=%d outside [0, n=%d]", K, g->n);
   if (K > 0 && (!out_seeds || !out_sigma_R)) return fail(IM_EINVAL, "null output");
   QueryParams q;
-  int rc = make_params(g, R, p, rng_seed, &q);
+  int rc = make_params_ex(g, R, p, rng_seed, flags & ~(uint32_t)IM_ALGO_FUSED_SAMPLING, &q);
   if (rc != IM_OK) return rc;
   if (K == 0) return IM_OK;
   std::lock_guard<std::mutex> lock(g->mu);
@@ -630,6 +870,8 @@ int im_select_seeds(const im_graph *g_, int32_t K, int32_t R, double p, uint32_t
   rc = internal_ws(g, R, &ws);
   if (rc != IM_OK) return rc;
   cudaStream_t s = t_stream;
+  if (flags & IM_ALGO_FUSED_SAMPLING)
+    return fused_sampling_select(g, ws, K, q, out_seeds, out_sigma_R, s);
   rc = enqueue_select(g, ws, K, q, nullptr, ws->d_seeds_out, ws->d_sigma_out, s, false);
   if (rc != IM_OK) return rc;
   API_CUDA(cudaMemcpyAsync(out_seeds, ws->d_seeds_out, sizeof(int32_t) * K,
@@ -639,8 +881,13 @@ int im_select_seeds(const im_graph *g_, int32_t K, int32_t R, double p, uint32_t
   return take_status(ws, s);
 }
 
-int im_estimate_spread(const im_graph *g_, const int32_t *seeds, int32_t num_seeds, int32_t R,
-                       double p, uint32_t rng_seed, uint64_t *out_sigma_R) {
+int im_select_seeds(const im_graph *g, int32_t K, int32_t R, double p, uint32_t rng_seed,
+                    int32_t *out_seeds, uint64_t *out_sigma_R) {
+  return im_select_seeds_ex(g, K, R, p, rng_seed, 0u, out_seeds, out_sigma_R);
+}
+
+int im_estimate_spread_ex(const im_graph *g_, const int32_t *seeds, int32_t num_seeds, int32_t R,
+                          double p, uint32_t rng_seed, uint32_t flags, uint64_t *out_sigma_R) {
   if (!g_) return fail(IM_EINVAL, "null graph");
   im_graph *g = const_cast<im_graph *>(g_);
   if (num_seeds < 0) return fail(IM_EINVAL, "num_seeds < 0");
@@ -648,7 +895,7 @@ int im_estimate_spread(const im_graph *g_, const int32_t *seeds, int32_t num_see
   for (int32_t i = 0; i < num_seeds; ++i)
     if (seeds[i] < 0 || seeds[i] >= g->n) return fail(IM_EINVAL, "seed id %d out of range", seeds[i]);
   QueryParams q;
-  int rc = make_params(g, R, p, rng_seed, &q);
+  int rc = make_params_ex(g, R, p, rng_seed, flags, &q);
   if (rc != IM_OK) return rc;
   std::lock_guard<std::mutex> lock(g->mu);
   DeviceGuard dg(g->device);
@@ -666,6 +913,11 @@ int im_estimate_spread(const im_graph *g_, const int32_t *seeds, int32_t num_see
   API_CUDA(cudaMemcpyAsync(out_sigma_R, ws->d_sigma_out, sizeof(uint64_t),
                            cudaMemcpyDeviceToHost, s), "copy sigma");
   return take_status(ws, s);
+}
+
+int im_estimate_spread(const im_graph *g, const int32_t *seeds, int32_t num_seeds, int32_t R,
+                       double p, uint32_t rng_seed, uint64_t *out_sigma_R) {
+  return im_estimate_spread_ex(g, seeds, num_seeds, R, p, rng_seed, 0u, out_sigma_R);
 }
 
 // Same kernels and launches as im_estimate_spread; every device buffer is a
@@ -711,11 +963,12 @@ int im_estimate_spread_noalloc(const im_graph *g, const int32_t *seeds, int32_t 
 // ------------------------------------------------------------------ test hooks
 
 static int debug_tables(const im_graph *g_, int32_t R, double p, uint32_t rng_seed,
-                        const uint8_t *h_mask, int32_t *out_labels, uint32_t *out_sizes) {
+                        const uint8_t *h_mask, int32_t *out_labels, uint32_t *out_sizes,
+                        uint32_t flags = 0u) {
   if (!g_) return fail(IM_EINVAL, "null graph");
   im_graph *g = const_cast<im_graph *>(g_);
   QueryParams q;
-  int rc = make_params(g, R, p, rng_seed, &q);
+  int rc = make_params_ex(g, R, p, rng_seed, flags, &q);
   if (rc != IM_OK) return rc;
   std::lock_guard<std::mutex> lock(g->mu);
   DeviceGuard dg(g->device);
@@ -754,6 +1007,12 @@ static int debug_tables(const im_graph *g_, int32_t R, double p, uint32_t rng_se
   if (d_siz) cudaFree(d_siz);
   if (e != cudaSuccess) return cuda_fail(e, "debug tables");
   return take_status(ws, s);
+}
+
+int im_debug_tables_ex(const im_graph *g, int32_t R, double p, uint32_t rng_seed, uint32_t flags,
+                       int32_t *out_labels, uint32_t *out_sizes) {
+  if (!out_labels && !out_sizes) return fail(IM_EINVAL, "null outputs");
+  return debug_tables(g, R, p, rng_seed, nullptr, out_labels, out_sizes, flags);
 }
 
 int im_debug_labels(const im_graph *g, int32_t R, double p, uint32_t rng_seed,
@@ -825,7 +1084,7 @@ int im_debug_first_gains(const im_graph *g_, int32_t R, double p, uint32_t rng_s
   cudaStream_t s = t_stream;
   rc = enqueue_select(g, ws, 0, q, nullptr, nullptr, nullptr, s, true);
   if (rc != IM_OK) return rc;
-  API_CUDA(launch_gains(g, ws, q, s), "k_gains");
+  API_CUDA(timed(IM_PHASE_GAINS, s, [&] { return launch_gains(g, ws, q, s); }), "k_gains");
   std::vector<uint64_t> keys((size_t)g->n);
   API_CUDA(cudaMemcpyAsync(keys.data(), ws->d_keys, sizeof(uint64_t) * g->n,
                            cudaMemcpyDeviceToHost, s), "copy keys");

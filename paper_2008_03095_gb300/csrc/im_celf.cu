@@ -1058,6 +1058,8 @@ cudaError_t launch_celf(const im_graph *g, const im_workspace *ws, const QueryPa
   // spent ~n/64 evaluations without committing.
   uint32_t ra = (uint32_t)g->n / 64;
   if (ra < (uint32_t)(4 * a.B)) ra = (uint32_t)(4 * a.B);
+  const int64_t ra_ovr = override_value(IM_OVR_CELF_REFRESH_AFTER);
+  if (ra_ovr > 0) ra = ra_ovr < (int64_t)UINT32_MAX ? (uint32_t)ra_ovr : UINT32_MAX;
   a.refresh_after = ra;
   a.magic_R = q.R == 1 ? 0u : (uint32_t)(((1ull << 32) + q.R - 1) / q.R);
   // Every round evaluates at least one candidate, fewer than refresh_after

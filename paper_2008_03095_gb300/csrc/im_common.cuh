@@ -31,7 +31,12 @@ struct QueryParams {
   int all_live;      // T == 2^32
   int none_live;     // T == 0
   int nb;            // lane-bucket bits: the top nb bits of X and h must agree for a live lane
+  int weighted;      // per-edge threshold codes of the graph replace T (w(u,v) of Eq. 2)
+  int mix;           // mixed hash: fmix32(X ^ h) is compared instead of X ^ h
 };
+
+// Threshold code of an always-live edge (w >= 1 - 2^-32).
+constexpr uint32_t kCodeAll = 0xffffffffu;
 
 // ------------------------------------------------------------------ device helpers
 __device__ __forceinline__ uint32_t rotl32(uint32_t x, int r) { return __funnelshift_l(x, x, r); }
@@ -77,6 +82,52 @@ __device__ __forceinline__ bool lane_live(uint32_t x, uint32_t h, uint32_t T32, 
 // live for hash h lies in bucket h >> (32 - nb).
 __device__ __forceinline__ uint32_t lane_bucket(uint32_t v, int nb) {
   return nb ? (v >> (32 - nb)) : 0u;
+}
+
+// MurmurHash3's avalanche finalizer (fmix32), the mixing step of the
+// mixed-hash sampler.
+__device__ __forceinline__ uint32_t fmix32(uint32_t h) {
+  h ^= h >> 16;
+  h *= 0x85ebca6bu;
+  h ^= h >> 13;
+  h *= 0xc2b2ae35u;
+  h ^= h >> 16;
+  return h;
+}
+
+// Live test under every sampling option: uniform T (T32 / all_live) or the
+// edge's threshold code c (weighted), on X ^ h or, mixed, on fmix32(X ^ h).
+__device__ __forceinline__ bool lane_live_opt(uint32_t x, uint32_t h, uint32_t T32, int all_live,
+                                              int weighted, uint32_t c, int mix) {
+  uint32_t z = x ^ h;
+  if (mix) z = fmix32(z);
+  if (weighted) return c == kCodeAll || z < c;
+  return all_live || z < T32;
+}
+
+// Candidate lanes [j0, j1) of an edge with hash h: the lanes are sorted by the
+// top nb bits of X (nb = kMaxBucketBits for weighted queries, 0 when mixed).
+// Uniform T: the lanes of bucket h >> (32 - nb). Weighted, code c: a live
+// lane has X ^ h <= c - 1, so the top clz(c - 1) bits of X equal those of h:
+// with at most kMaxBucketBits of them, a contiguous run of buckets.
+__device__ __forceinline__ void edge_lanes(uint32_t h, int nb, int weighted, uint32_t c, int mix,
+                                           const uint32_t *boff, uint32_t &j0, uint32_t &j1) {
+  if (mix || !weighted) {
+    const uint32_t b = mix ? 0u : lane_bucket(h, nb);
+    j0 = boff[b];
+    j1 = boff[b + 1];
+    return;
+  }
+  if (c == 0u) {  // never live
+    j0 = j1 = 0u;
+    return;
+  }
+  int eb = (c == kCodeAll) ? 0 : __clz(c - 1u);
+  if (eb > nb) eb = nb;
+  const int shift = nb - eb;
+  const uint32_t lo = (eb ? (h >> (32 - eb)) : 0u) << shift;
+  j0 = boff[lo];
+  j1 = boff[lo + (1u << shift)];
 }
 
 __device__ __forceinline__ void set_status(int32_t *status, int32_t code) {
@@ -142,6 +193,8 @@ struct im_graph {
   int32_t *d_eu = nullptr;  // upper-triangle edge list, eu[e] < ev[e]
   int32_t *d_ev = nullptr;
   int64_t m_up = 0;
+  uint32_t *d_code_up = nullptr;   // weighted graphs: threshold code per upper edge (eu/ev order)
+  uint32_t *d_code_arc = nullptr;  // weighted graphs: threshold code per CSR arc (d_adj order)
   std::mutex mu;            // serializes blocking calls on the internal workspace
   im_workspace *ws = nullptr;
 };
@@ -217,9 +270,14 @@ cudaError_t launch_celf(const im_graph *g, const im_workspace *ws, const QueryPa
 cudaError_t launch_spread(const im_graph *g, const im_workspace *ws, const QueryParams &q,
                           const int32_t *d_seeds, int num_seeds, const uint8_t *d_mask,
                           uint64_t *d_sigma, cudaStream_t s);
+// FusedSampling variant: single-lane table reset and mg accumulation
+cudaError_t launch_fs_init(const im_graph *g, int32_t *P1, cudaStream_t s);
+cudaError_t launch_fs_accum(const im_graph *g, const int32_t *P1, unsigned long long *mg,
+                            cudaStream_t s);
 // graph construction (blocking helpers, return IM_* codes)
+// h_w: per-arc probabilities (host, 2m) or null; validated by the caller.
 int graph_build_device(im_graph *g, const int32_t *h_xadj, const int32_t *h_adj,
-                       char *err, size_t errlen);
+                       const double *h_w, char *err, size_t errlen);
 
 // shared-memory need of the CELF kernel for a given R (pool in smem or spilled)
 int celf_pool_size(uint32_t R);

@@ -1,6 +1,8 @@
 // Device CSR store (Section 3.4): validation of a symmetric CSR and the
 // upper-triangle edge list {u < v} consumed by the component kernel.
 #include <algorithm>
+#include <cmath>
+#include <utility>
 #include <cstdio>
 #include <cstring>
 #include <vector>
@@ -74,8 +76,10 @@ __global__ void k_check_sym(const int32_t *xadj, const int32_t *adj, int32_t n, 
 }
 
 // warp per vertex: the upper neighbours of u are the sorted suffix v > u
+// (weighted graphs: the threshold code of each upper arc goes along)
 __global__ void k_scatter_upper(const int32_t *xadj, const int32_t *adj, int32_t n,
-                                const int32_t *upoff, int32_t *eu, int32_t *ev) {
+                                const int32_t *upoff, int32_t *eu, int32_t *ev,
+                                const uint32_t *code_arc, uint32_t *code_up) {
   const int lane = threadIdx.x & 31;
   const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -90,6 +94,7 @@ __global__ void k_scatter_upper(const int32_t *xadj, const int32_t *adj, int32_t
     for (int32_t a = lo + lane; a < end; a += 32) {
       eu[o + (a - lo)] = (int32_t)u;
       ev[o + (a - lo)] = adj[a];
+      if (code_up) code_up[o + (a - lo)] = code_arc[a];
     }
   }
 }
@@ -110,8 +115,15 @@ static int fail(char *err, size_t len, int code, const char *msg) {
     }                                                                                \
   } while (0)
 
-int graph_build_device(im_graph *g, const int32_t *h_xadj, const int32_t *h_adj, char *err,
-                       size_t errlen) {
+// Threshold code of an edge probability w in [0, 1]: T = floor(w * 2^32) of
+// Eq. 2, with the largest 32-bit code standing for an always-live edge.
+static uint32_t edge_code(double w) {
+  const double t = std::floor(w * 4294967296.0);
+  return t >= 4294967295.0 ? 0xffffffffu : (uint32_t)t;
+}
+
+int graph_build_device(im_graph *g, const int32_t *h_xadj, const int32_t *h_adj,
+                       const double *h_w, char *err, size_t errlen) {
   int rc = IM_OK;
   const int32_t n = g->n;
   const int64_t arcs = 2 * g->m;
@@ -145,6 +157,24 @@ int graph_build_device(im_graph *g, const int32_t *h_xadj, const int32_t *h_adj,
     rc = fail(err, errlen, IM_EINVAL, "neighbour id out of range [0, n)");
     goto done;
   }
+  if (h_w) {  // per-arc threshold codes, in the device's arc order
+    std::vector<uint32_t> codes((size_t)arcs);
+    for (int64_t a = 0; a < arcs; ++a) codes[(size_t)a] = edge_code(h_w[a]);
+    if (flags & kUnsorted) {  // neighbour lists get sorted below: carry the codes along
+      std::vector<std::pair<int32_t, uint32_t>> pr;
+      for (int32_t u = 0; u < n; ++u) {
+        pr.clear();
+        for (int32_t a = h_xadj[u]; a < h_xadj[u + 1]; ++a) pr.emplace_back(h_adj[a], codes[a]);
+        std::sort(pr.begin(), pr.end());
+        for (size_t k = 0; k < pr.size(); ++k) codes[(size_t)h_xadj[u] + k] = pr[k].second;
+      }
+    }
+    GB_CUDA(dev_malloc(reinterpret_cast<void **>(&g->d_code_arc),
+                       sizeof(uint32_t) * (size_t)(arcs > 0 ? arcs : 1)), "cudaMalloc codes");
+    if (arcs > 0)
+      GB_CUDA(cudaMemcpy(g->d_code_arc, codes.data(), sizeof(uint32_t) * (size_t)arcs,
+                         cudaMemcpyHostToDevice), "copy codes");
+  }
   if (flags & kUnsorted) {  // sort every neighbour list once, on the host
     std::vector<int32_t> sorted(h_adj, h_adj + arcs);
     for (int32_t u = 0; u < n; ++u) std::sort(sorted.begin() + h_xadj[u], sorted.begin() + h_xadj[u + 1]);
@@ -172,7 +202,11 @@ int graph_build_device(im_graph *g, const int32_t *h_xadj, const int32_t *h_adj,
             "copy offsets");
     GB_CUDA(dev_malloc(reinterpret_cast<void **>(&g->d_eu), sizeof(int32_t) * (size_t)m_up), "cudaMalloc eu");
     GB_CUDA(dev_malloc(reinterpret_cast<void **>(&g->d_ev), sizeof(int32_t) * (size_t)m_up), "cudaMalloc ev");
-    k_scatter_upper<<<wblocks, 256>>>(g->d_xadj, g->d_adj, n, d_up, g->d_eu, g->d_ev);
+    if (h_w)
+      GB_CUDA(dev_malloc(reinterpret_cast<void **>(&g->d_code_up), sizeof(uint32_t) * (size_t)m_up),
+              "cudaMalloc upper codes");
+    k_scatter_upper<<<wblocks, 256>>>(g->d_xadj, g->d_adj, n, d_up, g->d_eu, g->d_ev,
+                                      g->d_code_arc, g->d_code_up);
     GB_CUDA(cudaGetLastError(), "k_scatter_upper");
   }
   GB_CUDA(cudaDeviceSynchronize(), "graph build");

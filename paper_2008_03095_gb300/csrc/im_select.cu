@@ -207,12 +207,17 @@ struct UnionArgs {
   uint32_t cap;
   int32_t *P;
   int32_t *status;
+  // sampling options: per-edge codes (weighted), mixed hash
+  int weighted, mix;
+  const uint32_t *code_up;
   // explicit-mask mode (test hook)
   const uint8_t *mask;
   const int32_t *xadj, *adj;
 };
 
-template <bool MASKED>
+// OPTS: the sampling options (per-edge threshold codes, mixed hash) are in
+// play; the uniform-p path keeps its own instantiation.
+template <bool MASKED, bool OPTS>
 __global__ void __launch_bounds__(256) k_union(UnionArgs a) {
   extern __shared__ uint32_t s_boff[];
   if (!MASKED) {
@@ -227,12 +232,18 @@ __global__ void __launch_bounds__(256) k_union(UnionArgs a) {
     const int64_t e = base + lane;
     const bool valid = e < a.m_up;
     int32_t u = 0, v = 0;
-    uint32_t h = 0, j0 = 0, c = 0;
+    uint32_t h = 0, j0 = 0, c = 0, code = 0;
     if (valid) {
       u = a.eu[e];
       v = a.ev[e];
       if (MASKED) {
         c = a.R;
+      } else if (OPTS) {
+        h = edge_hash_ordered((uint32_t)u, (uint32_t)v);
+        if (a.weighted) code = a.code_up[e];
+        uint32_t j1;
+        edge_lanes(h, a.nb, a.weighted, code, a.mix, s_boff, j0, j1);
+        c = j1 - j0;
       } else {
         h = edge_hash_ordered((uint32_t)u, (uint32_t)v);
         const uint32_t b = lane_bucket(h, a.nb);
@@ -263,6 +274,7 @@ __global__ void __launch_bounds__(256) k_union(UnionArgs a) {
       const uint32_t s_h = __shfl_sync(kFull, h, pos);
       const int32_t s_u = __shfl_sync(kFull, u, pos);
       const int32_t s_v = __shfl_sync(kFull, v, pos);
+      const uint32_t s_code = OPTS ? __shfl_sync(kFull, code, pos) : 0u;
       if (item < total) {
         const uint32_t j = s_j0 + (item - (s_incl - s_c));
         bool live;
@@ -273,6 +285,9 @@ __global__ void __launch_bounds__(256) k_union(UnionArgs a) {
             if (a.adj[mid] < s_v) lo = mid + 1; else hi = mid;
           }
           live = a.mask[(uint64_t)lo * a.R + j] != 0;
+        } else if (OPTS) {
+          live = lane_live_opt(__ldg(a.Xs + j), s_h, a.T32, a.all_live, a.weighted, s_code,
+                               a.mix);
         } else {
           live = lane_live(__ldg(a.Xs + j), s_h, a.T32, a.all_live);
         }
@@ -301,15 +316,21 @@ cudaError_t launch_union(const im_graph *g, const im_workspace *ws, const QueryP
   a.mask = d_mask;
   a.xadj = g->d_xadj;
   a.adj = g->d_adj;
+  a.weighted = q.weighted;
+  a.mix = q.mix;
+  a.code_up = g->d_code_up;
   int64_t warps_needed = (g->m_up + 31) / 32;
   int64_t blocks = (warps_needed + 7) / 8;
   int64_t cap = (int64_t)g->num_sms * 8;
   if (blocks > cap) blocks = cap;
   if (d_mask) {
-    k_union<true><<<(unsigned)blocks, 256, 0, s>>>(a);
+    k_union<true, false><<<(unsigned)blocks, 256, 0, s>>>(a);
   } else {
     size_t smem = ((1u << q.nb) + 1) * sizeof(uint32_t);
-    k_union<false><<<(unsigned)blocks, 256, smem, s>>>(a);
+    if (q.weighted || q.mix)
+      k_union<false, true><<<(unsigned)blocks, 256, smem, s>>>(a);
+    else
+      k_union<false, false><<<(unsigned)blocks, 256, smem, s>>>(a);
   }
   return cudaGetLastError();
 }

@@ -47,6 +47,8 @@ struct SpreadArgs {
   int32_t *status;
   unsigned long long *stats;
   uint32_t level_cap;    // budget of BFS levels (a BFS has at most n levels)
+  int weighted, mix;     // sampling options: per-arc codes, mixed hash
+  const uint32_t *code_arc;
 };
 
 template <class T>
@@ -77,8 +79,10 @@ __device__ __forceinline__ void push_frontier(const SpreadArgs &a, int32_t v, ui
 // Live lanes among the frontier lanes f of word w (Eq. 2), two lanes per
 // step so that their loads of X overlap; xs is the shared-memory copy of the
 // lane randoms or the global one.
+template <bool OPTS>
 __device__ __forceinline__ uint32_t live_lanes(uint32_t f, uint32_t w, const uint32_t *xs,
-                                               uint32_t h, uint32_t T32, int all_live) {
+                                               uint32_t h, uint32_t T32, int all_live,
+                                               int weighted, uint32_t code, int mix) {
   uint32_t nbits = 0;
   while (f) {
     const int b0 = __ffs(f) - 1;
@@ -87,8 +91,13 @@ __device__ __forceinline__ uint32_t live_lanes(uint32_t f, uint32_t w, const uin
     f &= f - 1;
     const uint32_t x0 = xs[(w << 5) + (uint32_t)b0];
     const uint32_t x1 = xs[(w << 5) + (uint32_t)b1];
-    nbits |= (uint32_t)lane_live(x0, h, T32, all_live) << b0;
-    nbits |= (uint32_t)lane_live(x1, h, T32, all_live) << b1;
+    if (OPTS) {
+      nbits |= (uint32_t)lane_live_opt(x0, h, T32, all_live, weighted, code, mix) << b0;
+      nbits |= (uint32_t)lane_live_opt(x1, h, T32, all_live, weighted, code, mix) << b1;
+    } else {
+      nbits |= (uint32_t)lane_live(x0, h, T32, all_live) << b0;
+      nbits |= (uint32_t)lane_live(x1, h, T32, all_live) << b1;
+    }
   }
   return nbits;
 }
@@ -97,6 +106,7 @@ __device__ __forceinline__ uint32_t live_lanes(uint32_t f, uint32_t w, const uin
 // frontier-bit tests then read them there instead of through L1.
 constexpr uint32_t kSpreadSmemLanes = 8192;
 
+template <bool OPTS>
 __global__ void __launch_bounds__(512) k_spread(SpreadArgs a) {
   extern __shared__ uint32_t sXs[];
   cg::grid_group grid = cg::this_grid();
@@ -180,12 +190,16 @@ __global__ void __launch_bounds__(512) k_spread(SpreadArgs a) {
       const int32_t beg = a.xadj[u], end = a.xadj[u + 1];
       const int32_t e = beg + (int32_t)(ch << 5) + lane;
       int32_t v = -1;
-      uint32_t j0 = 0, j1 = 0, h = 0;
+      uint32_t j0 = 0, j1 = 0, h = 0, code = 0;
       if (e < end) {
         v = a.adj[e];
         if (v != u) {
           if (a.mask) {
             j1 = a.R;
+          } else if (OPTS) {
+            h = edge_hash(u, v);
+            if (a.weighted) code = __ldg(a.code_arc + e);
+            edge_lanes(h, a.nb, a.weighted, code, a.mix, a.boff, j0, j1);
           } else {
             h = edge_hash(u, v);
             const uint32_t b = lane_bucket(h, a.nb);
@@ -224,9 +238,9 @@ __global__ void __launch_bounds__(512) k_spread(SpreadArgs a) {
             nbits |= (uint32_t)(a.mask[(uint64_t)e * a.R + (w << 5) + (uint32_t)bit] != 0) << bit;
           }
         } else if (a.xs_smem) {
-          nbits = live_lanes(f, w, sXs, h, a.T32, a.all_live);
+          nbits = live_lanes<OPTS>(f, w, sXs, h, a.T32, a.all_live, a.weighted, code, a.mix);
         } else {
-          nbits = live_lanes(f, w, a.Xs, h, a.T32, a.all_live);
+          nbits = live_lanes<OPTS>(f, w, a.Xs, h, a.T32, a.all_live, a.weighted, code, a.mix);
         }
         if (!nbits) continue;
         const uint64_t o = (uint64_t)v * W + w;
@@ -323,13 +337,18 @@ cudaError_t launch_spread(const im_graph *g, const im_workspace *ws, const Query
   a.out = d_sigma;
   a.status = ws->d_status;
   a.stats = ws->d_stats;
+  a.weighted = q.weighted;
+  a.mix = q.mix;
+  a.code_arc = g->d_code_arc;
   a.level_cap = (uint32_t)g->n + 2u;
   const int64_t lo = override_value(IM_OVR_SPREAD_LEVEL_CAP);
   if (lo > 0 && (uint64_t)lo < a.level_cap) a.level_cap = (uint32_t)lo;
   a.xs_smem = (!d_mask && q.R <= kSpreadSmemLanes) ? 1 : 0;
   const size_t smem = a.xs_smem ? (size_t)q.R * sizeof(uint32_t) : 0;
+  const void *fn = (!d_mask && (q.weighted || q.mix)) ? (const void *)k_spread<true>
+                                                       : (const void *)k_spread<false>;
   int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spread, 512, smem);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 512, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   if (per_sm > 2) per_sm = 2;
@@ -338,7 +357,7 @@ cudaError_t launch_spread(const im_graph *g, const im_workspace *ws, const Query
   if ((uint64_t)g->n * a.W < (4u << 20)) per_sm = 1;
   dim3 grid(g->num_sms * per_sm), block(512);
   void *args[] = {&a};
-  return cudaLaunchCooperativeKernel((const void *)k_spread, grid, block, args, smem, s);
+  return cudaLaunchCooperativeKernel(fn, grid, block, args, smem, s);
 }
 
 }  // namespace imgb

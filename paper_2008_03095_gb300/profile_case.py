@@ -1,0 +1,58 @@
+"""Run the bandwidth kernels of one workload query for a profiler, without the
+lazy greedy: the component pipeline up to the first-seed gains (k_prep,
+k_union, k_compress, k_gains through im_debug_first_gains) and the spread of
+a fixed seed set (k_prep, k_spread through im_estimate_spread), each
+`--repeat` times on one resident graph.
+
+    python -m paper_2008_03095_gb300.profile_case --workload powerlaw_n37154 --p 0.05
+
+The seed set of the spread is the K highest-degree vertices (lowest id first
+on equal degree). Prints one JSON line with the per-phase event times.
+"""
+import argparse
+import json
+import os
+import sys
+
+import numpy as np
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", default="powerlaw_n37154")
+    ap.add_argument("--p", type=float, default=None)
+    ap.add_argument("--repeat", type=int, default=2)
+    ap.add_argument("--no-spread", action="store_true")
+    args = ap.parse_args(argv)
+
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import torch
+
+    import paper_2008_03095_gb300 as im
+    from paper_2008_03095_gb300 import build, synth
+
+    build.build()
+    w = synth.WORKLOADS[args.workload]
+    p = w["ps"][-1] if args.p is None else args.p
+    R, K, seed = w["R"], w["K"], w["rng_seed"]
+    xadj, adj = synth.workload_graph(args.workload)
+    deg = np.diff(xadj)
+    seeds = np.argsort(-deg, kind="stable")[:K].astype(np.int32)
+    torch.cuda.set_device(0)
+    g = im.im_graph_create(xadj, adj)
+    im.im_profile_enable(True)
+    for _ in range(args.repeat):
+        mg = im.im_debug_first_gains(g, R, p, seed)
+        if not args.no_spread:
+            im.im_estimate_spread(g, seeds, R, p, seed)
+    prof = im.im_profile_read()
+    im.im_profile_enable(False)
+    g.close()
+    print(json.dumps({"workload": args.workload, "p": p, "R": R, "repeat": args.repeat,
+                      "max_first_gain": int(mg.max()),
+                      "avg_us": {k: round(v[0] / v[1] * 1e3, 2) for k, v in prof.items() if v[1]}}))
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

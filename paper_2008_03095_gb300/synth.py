@@ -146,6 +146,25 @@ def random_graph(n, m, seed):
     return _finish(rng, n, lo, hi)
 
 
+def edge_weights(xadj, adj, kind, seed):
+    """One probability per CSR arc, equal on both arcs of an edge, drawn per
+    undirected edge (numpy PCG64) as in the paper's weight settings (Section
+    4): "uniform" U[0, 0.1] or "normal" N(0.05, 0.025) clipped to [0, 1]."""
+    n = xadj.shape[0] - 1
+    src = np.repeat(np.arange(n, dtype=np.int64), np.diff(xadj))
+    dst = adj.astype(np.int64)
+    key = np.minimum(src, dst) * n + np.maximum(src, dst)
+    uniq, inv = np.unique(key, return_inverse=True)
+    rng = _rng(seed)
+    if kind == "uniform":
+        vals = rng.uniform(0.0, 0.1, size=uniq.shape[0])
+    elif kind == "normal":
+        vals = np.clip(rng.normal(0.05, 0.025, size=uniq.shape[0]), 0.0, 1.0)
+    else:
+        raise ValueError("unknown weight setting %r" % kind)
+    return vals[inv].astype(np.float64)
+
+
 # Workload recipes: graph builder, its arguments, and the query parameters.
 WORKLOADS = {
     # n=2,000 m=8,000 power-law (exponent 2.5)
