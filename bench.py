@@ -270,10 +270,11 @@ def celf_method_bytes(n, R, evaluations, extractions):
     return evaluations * (4 * R + 4 * R + R / 8) + extractions * 8 * n
 
 
-def celf_refresh_bytes(n, R, refreshes):
-    """Bytes of the dense refreshes (every vertex re-evaluated), a choice of
-    this design rather than work the method requires."""
-    return refreshes * (n * (4 * R + 4 * R + R / 8) + 8 * n)
+def celf_refresh_bytes(n, R, refreshes, refreshed):
+    """Bytes of the bound refreshes, a choice of this design rather than work
+    the method requires: each scans the n bounds and chosen flags, and the
+    vertices whose bound reaches the best known exact gain are re-evaluated."""
+    return refreshed * (4 * R + 4 * R + R / 8) + refreshes * 9 * n
 
 
 def g_m_up(xadj, adj):
@@ -455,7 +456,8 @@ def measure(name, w, xadj, adj, steps, warmup, world, detail):
         q = [by_p[str(p)]["per_query"] for p in ps]
         mb = statistics.mean(celf_method_bytes(n, R, x["celf_evaluations"], x["celf_extractions"])
                              for x in q)
-        rb = statistics.mean(celf_refresh_bytes(n, R, x["celf_refreshes"]) for x in q)
+        rb = statistics.mean(celf_refresh_bytes(n, R, x["celf_refreshes"], x["celf_refreshed"])
+                             for x in q)
         roof.update(bytes_per_launch=mb, refresh_bytes_per_launch=rb,
                     achieved=mb / avg_s / 1e9,
                     note="method bytes only (exact gain evaluations E*(8R + R/8) plus prefix "

@@ -195,6 +195,71 @@ int im_estimate_spread_ex_async(const im_graph *g, im_workspace *ws, const int32
                                 int32_t num_seeds, int32_t R, double p, uint32_t rng_seed,
                                 uint32_t flags, uint64_t *d_sigma_R);
 
+/* ---------------------------------------------------------------- batches
+ * Many independent select queries -- each its own graph, K, R, p, options --
+ * in ONE persistent kernel launch: the steps of Algorithm 7 (lane randoms,
+ * label init, fused sample + union, size memo, first gains, lazy greedy) are
+ * cut into work items (query, phase, tile) that the blocks of the launch take
+ * in phase order from a device queue, waiting with an iteration budget for
+ * the items they depend on. Every query's seeds and sigma*R are those of
+ * im_select_seeds_ex on its own. The launch is an ordinary one (no
+ * co-residency needed), so im_batch_run_async can be captured in a CUDA graph.
+ * The tiling of each query's work (label slots, edges, size-memo tiles and
+ * vertices per item) comes from the autotuner's cache for the query's size
+ * class, or a default; im_batch_autotune fills the cache by timing.
+ * All graphs of a batch are on one device; graphs must outlive the batch. */
+typedef struct im_batch im_batch; /* opaque, library-owned */
+typedef struct {
+  int32_t graph;     /* index into the graphs array of im_batch_create */
+  int32_t K;         /* 1 <= K <= n */
+  int32_t R;         /* 1 <= R <= 16384 (a batch keeps the lane sort and pool on chip) */
+  double p;          /* as im_select_seeds (ignored with IM_SAMPLE_EDGE_WEIGHTS) */
+  uint32_t rng_seed;
+  uint32_t flags;    /* IM_SAMPLE_* */
+} im_batch_query;
+
+/* Validate the queries and allocate every query's tables in one device
+ * arena (n*R*4 + n*R/8 + 9n bytes and a few KB per query); host arrays are
+ * copied. Errors: IM_EINVAL, IM_ENOMEM (the arena does not fit). */
+int im_batch_create(const im_graph *const *graphs, int32_t num_graphs,
+                    const im_batch_query *queries, int32_t count, im_batch **out);
+int im_batch_destroy(im_batch *b);
+
+/* Queue one run of all queries on the thread's stream: three small resets
+ * and one persistent launch of one 1024-thread block per SM. Runs may repeat;
+ * each overwrites the results. */
+int im_batch_run_async(im_batch *b);
+
+/* Synchronize the thread's stream and copy the results to host arrays:
+ * out_seeds / out_sigma_R hold sum(K) entries, query i's K values at offset
+ * K_0 + ... + K_{i-1}; out_status (may be NULL) gets each query's device
+ * status (IM_OK, IM_ETIMEOUT, IM_EINTERNAL). Returns the first non-OK status. */
+int im_batch_results(im_batch *b, int32_t *out_seeds, uint64_t *out_sigma_R, int32_t *out_status);
+
+/* Work counters of one query of the last run (IM_STAT_* layout). */
+int im_batch_query_stats(im_batch *b, int32_t query, int64_t *out);
+
+enum {
+  IM_BATCH_INFO_QUERIES = 0,
+  IM_BATCH_INFO_ITEMS = 1,        /* work items of one run */
+  IM_BATCH_INFO_DEVICE_BYTES = 2, /* arena size */
+  IM_BATCH_INFO_TOTAL_K = 3,
+  IM_BATCH_INFO_LEVELS = 4,       /* histogram of tiling levels: 4 bits per level 0..4 */
+  IM_BATCH_INFO_COUNT = 5
+};
+int im_batch_info(const im_batch *b, int64_t *out);
+
+/* Autotune: for each size class (floor(log2(n*R)), R, flags) of the batch,
+ * time up to four of its largest queries as a batch of their own at each of
+ * five tiling granularities (trials timed runs each, after a warm-up) and keep
+ * the fastest in a process-wide cache; then re-plan b with it. Later batches
+ * of the same classes use the cache. The cache can be saved to and loaded
+ * from a text file. */
+int im_batch_autotune(im_batch *b, int32_t trials);
+int im_autotune_cache_save(const char *path);
+int im_autotune_cache_load(const char *path);
+int im_autotune_cache_clear(void);
+
 /* Synchronize the thread's stream and return (then clear) the first device
  * status recorded in ws since the last call: IM_OK, IM_EINVAL, IM_ETIMEOUT or
  * IM_EINTERNAL. */
@@ -214,7 +279,7 @@ enum {
   IM_STAT_CELF_REFRESHES = 8,    /* grid-wide recomputations of all exact gains */
   IM_STAT_CELF_CYC_COMMITS = 9,  /* ... in the commit loop (picks, pool updates) */
   IM_STAT_CELF_CYC_COVER = 10,   /* ... marking committed components covered */
-  IM_STAT_RESERVED_11 = 11,      /* 0 */
+  IM_STAT_CELF_REFRESHED = 11,   /* vertices re-evaluated by the refreshes */
   IM_STAT_RESERVED_12 = 12,      /* 0 */
   IM_STAT_CHECK_CODE = 13,       /* first failed internal invariant check (0 = none) */
   IM_STAT_CHECK_V0 = 14,         /* ... and two values describing it */

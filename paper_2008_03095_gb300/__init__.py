@@ -14,7 +14,11 @@ from ._binding import (IM_EBUSY, IM_ECUDA, IM_EINTERNAL, IM_EINVAL, IM_ENOMEM, I
                        IM_NUM_OVERRIDES, IM_SAMPLE_EDGE_WEIGHTS, IM_SAMPLE_MIXED_HASH,
                        IM_ALGO_FUSED_SAMPLING, im_graph_create_weighted, im_select_seeds_ex,
                        im_estimate_spread_ex, im_select_seeds_ex_async,
-                       im_estimate_spread_ex_async, im_debug_tables_ex,
+                       im_estimate_spread_ex_async, im_debug_tables_ex, Batch, BatchQuery,
+                       im_batch_create, im_batch_run_async, im_batch_results,
+                       im_batch_query_stats, im_batch_info, im_batch_autotune,
+                       im_batch_destroy, im_autotune_cache_save, im_autotune_cache_load,
+                       im_autotune_cache_clear, BATCH_INFO,
                        im_estimate_spread, im_estimate_spread_async, im_estimate_spread_noalloc,
                        im_graph_create, NOALLOC_LIMITS,
                        im_graph_create_raw, im_graph_destroy, im_graph_info, im_kernel_launches,

@@ -75,6 +75,16 @@ def lib():
         "im_debug_estimate_spread_masked": [P, P, i32, i32, P, P],
         "im_debug_override": [i32, i64],
         "im_graph_create_weighted": [i32, i64, P, P, P, P],
+        "im_batch_create": [P, i32, P, i32, P],
+        "im_batch_destroy": [P],
+        "im_batch_run_async": [P],
+        "im_batch_results": [P, P, P, P],
+        "im_batch_query_stats": [P, i32, P],
+        "im_batch_info": [P, P],
+        "im_batch_autotune": [P, i32],
+        "im_autotune_cache_save": [ctypes.c_char_p],
+        "im_autotune_cache_load": [ctypes.c_char_p],
+        "im_autotune_cache_clear": [],
         "im_debug_tables_ex": [P, i32, f64, u32, u32, P, P],
         "im_select_seeds_ex": [P, i32, i32, f64, u32, u32, P, P],
         "im_estimate_spread_ex": [P, P, i32, i32, f64, u32, u32, P],
@@ -304,7 +314,7 @@ def im_workspace_status(ws):
 
 STATS = ("celf_rounds", "celf_evaluations", "celf_extractions", "spread_levels",
          "celf_cycles_extract", "celf_cycles_eval", "celf_cycles_commit", "celf_cycles_merge",
-         "celf_refreshes", "celf_cycles_commits", "celf_cycles_cover", "reserved_11",
+         "celf_refreshes", "celf_cycles_commits", "celf_cycles_cover", "celf_refreshed",
          "reserved_12", "check_code", "check_v0", "check_v1")
 
 
@@ -441,3 +451,99 @@ def im_debug_estimate_spread_masked(g, seeds, mask):
     _check(lib().im_debug_estimate_spread_masked(_gh(g), _ptr(seeds), seeds.shape[0],
                                                  mask.shape[1], _ptr(mask), ctypes.byref(out)))
     return int(out.value)
+
+
+# ------------------------------------------------------------------ batches
+
+
+class BatchQuery(ctypes.Structure):
+    _fields_ = [("graph", ctypes.c_int32), ("K", ctypes.c_int32), ("R", ctypes.c_int32),
+                ("p", ctypes.c_double), ("rng_seed", ctypes.c_uint32), ("flags", ctypes.c_uint32)]
+
+
+class Batch:
+    """Owning wrapper of an im_batch handle; keeps its graphs alive."""
+
+    def __init__(self, handle, graphs, Ks):
+        self.handle = handle
+        self.graphs = graphs
+        self.Ks = list(Ks)
+
+    def close(self):
+        if self.handle:
+            _check(lib().im_batch_destroy(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def im_batch_create(graphs, queries):
+    """graphs: list of Graph; queries: list of dicts with keys graph, K, R, p,
+    rng_seed and optional flags."""
+    n = len(queries)
+    arr = (BatchQuery * n)()
+    for i, q in enumerate(queries):
+        arr[i] = BatchQuery(int(q["graph"]), int(q["K"]), int(q["R"]), float(q["p"]),
+                            int(q["rng_seed"]) & 0xFFFFFFFF, int(q.get("flags", 0)))
+    handles = (ctypes.c_void_p * len(graphs))(*[_gh(g).value if hasattr(_gh(g), "value")
+                                                else _gh(g) for g in graphs])
+    out = ctypes.c_void_p()
+    _check(lib().im_batch_create(handles, len(graphs), arr, n, ctypes.byref(out)))
+    return Batch(out, list(graphs), [int(q["K"]) for q in queries])
+
+
+def im_batch_run_async(b):
+    _check(lib().im_batch_run_async(b.handle))
+
+
+def im_batch_results(b, check=True):
+    """(list of seeds int32[K_i], list of sigmaR uint64[K_i], statuses int32[count])."""
+    total = sum(b.Ks)
+    seeds = np.empty(max(total, 1), dtype=np.int32)
+    sigma = np.empty(max(total, 1), dtype=np.uint64)
+    status = np.empty(len(b.Ks), dtype=np.int32)
+    rc = lib().im_batch_results(b.handle, _ptr(seeds), _ptr(sigma), _ptr(status))
+    if check:
+        _check(rc)
+    off = np.concatenate([[0], np.cumsum(b.Ks)])
+    return ([seeds[off[i]:off[i + 1]] for i in range(len(b.Ks))],
+            [sigma[off[i]:off[i + 1]] for i in range(len(b.Ks))], status)
+
+
+def im_batch_query_stats(b, query):
+    out = np.zeros(len(STATS), dtype=np.int64)
+    _check(lib().im_batch_query_stats(b.handle, query, _ptr(out)))
+    return {name: int(out[i]) for i, name in enumerate(STATS)}
+
+
+BATCH_INFO = ("queries", "items", "device_bytes", "total_K", "levels")
+
+
+def im_batch_info(b):
+    out = np.zeros(len(BATCH_INFO), dtype=np.int64)
+    _check(lib().im_batch_info(b.handle, _ptr(out)))
+    return {name: int(out[i]) for i, name in enumerate(BATCH_INFO)}
+
+
+def im_batch_autotune(b, trials=3):
+    _check(lib().im_batch_autotune(b.handle, trials))
+
+
+def im_batch_destroy(b):
+    b.close()
+
+
+def im_autotune_cache_save(path):
+    _check(lib().im_autotune_cache_save(path.encode()))
+
+
+def im_autotune_cache_load(path):
+    _check(lib().im_autotune_cache_load(path.encode()))
+
+
+def im_autotune_cache_clear():
+    _check(lib().im_autotune_cache_clear())

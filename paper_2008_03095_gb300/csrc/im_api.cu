@@ -160,23 +160,6 @@ int cuda_fail(cudaError_t e, const char *what) {
     if (e_ != cudaSuccess) return cuda_fail(e_, what); \
   } while (0)
 
-// Makes the graph's device current for the duration of a call.
-struct DeviceGuard {
-  int prev = -1;
-  bool ok = true;
-  explicit DeviceGuard(int dev) {
-    if (cudaGetDevice(&prev) != cudaSuccess) {
-      ok = false;
-      return;
-    }
-    if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
-  }
-  ~DeviceGuard() {
-    int cur = -1;
-    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-  }
-};
-
 int make_params(const im_graph *g, int32_t R, double p, uint32_t seed, QueryParams *q) {
   if (R < 1 || R > kMaxR) return fail(IM_EINVAL, "R=%d outside [1, %d]", R, kMaxR);
   if (!(p >= 0.0 && p <= 1.0)) return fail(IM_EINVAL, "p outside [0, 1] or NaN");
@@ -401,6 +384,35 @@ int ensure_seed_in(im_workspace *ws, int64_t count) {
   ws->seed_in_cap = count > 0 ? count : 1;
   return IM_OK;
 }
+
+}  // namespace
+
+namespace imgb {
+
+int api_error(int code, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  std::vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  t_err = buf;
+  return code;
+}
+
+int api_cuda_error(cudaError_t e, const char *what) { return cuda_fail(e, what); }
+
+cudaStream_t api_stream() { return t_stream; }
+
+void api_count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+int api_query_params(const im_graph *g, int32_t R, double p, uint32_t seed, uint32_t flags,
+                     QueryParams *q) {
+  return make_params_ex(g, R, p, seed, flags, q);
+}
+
+}  // namespace imgb
+
+namespace {
 
 // FusedSampling (Section 4, Table 4): MixGreedy with the paper's fused hash
 // sampling but none of its batching or memoization. Simulation r runs alone

@@ -248,6 +248,33 @@ cudaError_t dev_malloc(void **p, size_t bytes);
 // Union-find walk budget of a launch (uf_cap, or a smaller test override).
 uint32_t uf_budget(uint32_t n);
 
+// Makes the graph's device current for the duration of a call.
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = true;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) {
+      ok = false;
+      return;
+    }
+    if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+// ------------------------------------------------------------------ API internals
+// (defined in im_api.cu, used by the other host-side entry points)
+int api_error(int code, const char *fmt, ...);           // sets im_last_error, returns code
+int api_cuda_error(cudaError_t e, const char *what);     // IM_ENOMEM or IM_ECUDA
+cudaStream_t api_stream();                               // the calling thread's stream
+void api_count_launch();                                  // one more kernel in im_kernel_launches
+// Query parameters of R, p, rng_seed under the IM_SAMPLE_* flags (IM_EINVAL on bad input).
+int api_query_params(const im_graph *g, int32_t R, double p, uint32_t seed, uint32_t flags,
+                     QueryParams *q);
+
 // ------------------------------------------------------------------ launchers
 // All launchers queue work on `s` and return the launch error (if any).
 cudaError_t launch_prep(const im_workspace *ws, const QueryParams &q, bool init_table,

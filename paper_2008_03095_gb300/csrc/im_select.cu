@@ -17,66 +17,10 @@
 #include <cooperative_groups.h>
 
 #include "im_common.cuh"
+#include "im_lanes.cuh"
+#include "im_union.cuh"
 
 namespace imgb {
-
-// ------------------------------------------------------------------ MT19937
-// Matsumoto & Nishimura (1998), 32-bit: n = 624, m = 397, matrix 0x9908b0df,
-// tempering (11, 7 0x9d2c5680, 15 0xefc60000, 18), init multiplier 1812433253.
-// The state refresh ("twist") is done by one block in four dependency-safe
-// phases: entries [0,227) read only old state, [227,454) and [454,623) read
-// entries refreshed by the previous phase, and entry 623 reads entry 0.
-__device__ __forceinline__ uint32_t mt_next_word(uint32_t cur, uint32_t nxt, uint32_t far) {
-  uint32_t y = (cur & 0x80000000u) | (nxt & 0x7fffffffu);
-  return far ^ (y >> 1) ^ ((y & 1u) ? 0x9908b0dfu : 0u);
-}
-
-__device__ void mt_twist(uint32_t *mt) {
-  const int t = threadIdx.x;
-  uint32_t nv = 0;
-  if (t < 227) nv = mt_next_word(mt[t], mt[t + 1], mt[t + 397]);
-  __syncthreads();
-  if (t < 227) mt[t] = nv;
-  __syncthreads();
-  if (t < 227) nv = mt_next_word(mt[t + 227], mt[t + 228], mt[t]);
-  __syncthreads();
-  if (t < 227) mt[t + 227] = nv;
-  __syncthreads();
-  if (t < 169) nv = mt_next_word(mt[t + 454], mt[t + 455], mt[t + 227]);
-  __syncthreads();
-  if (t < 169) mt[t + 454] = nv;
-  __syncthreads();
-  if (t == 0) mt[623] = mt_next_word(mt[623], mt[0], mt[396]);
-  __syncthreads();
-}
-
-__device__ __forceinline__ uint32_t mt_temper(uint32_t y) {
-  y ^= y >> 11;
-  y ^= (y << 7) & 0x9d2c5680u;
-  y ^= (y << 15) & 0xefc60000u;
-  y ^= y >> 18;
-  return y;
-}
-
-// Ascending bitonic sort of npow2 keys (shared or global memory) by one block.
-__device__ void block_bitonic_sort(uint32_t *a, int npow2) {
-  for (int k = 2; k <= npow2; k <<= 1) {
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      for (int i = threadIdx.x; i < npow2; i += blockDim.x) {
-        int ixj = i ^ j;
-        if (ixj > i) {
-          uint32_t x = a[i], y = a[ixj];
-          bool up = (i & k) == 0;
-          if ((x > y) == up) {
-            a[i] = y;
-            a[ixj] = x;
-          }
-        }
-      }
-      __syncthreads();
-    }
-  }
-}
 
 struct PrepArgs {
   // lanes
@@ -92,49 +36,7 @@ struct PrepArgs {
 };
 
 __device__ void prep_lanes(const PrepArgs &a, uint32_t *s_sort) {
-  __shared__ uint32_t mt[624];
-  const int t = threadIdx.x;
-  if (t == 0) {  // the seeding recurrence is sequential; keep it in a register
-    uint32_t x = a.seed;
-    mt[0] = x;
-    for (int i = 1; i < 624; ++i) {
-      x = 1812433253u * (x ^ (x >> 30)) + (uint32_t)i;
-      mt[i] = x;
-    }
-  }
-  __syncthreads();
-  for (uint32_t base = 0; base < a.R; base += 624) {
-    mt_twist(mt);
-    for (uint32_t i = t; i < 624 && base + i < a.R; i += blockDim.x) a.X[base + i] = mt_temper(mt[i]);
-    __syncthreads();
-  }
-  // Lane order: sort keys (bucket << 16 | r); a stable, deterministic order.
-  int npow2 = 1;
-  while (npow2 < (int)a.R) npow2 <<= 1;
-  uint32_t *keys = (npow2 <= kSortSmemMax) ? s_sort : a.sortbuf;
-  for (int i = t; i < npow2; i += blockDim.x)
-    keys[i] = (i < (int)a.R) ? ((lane_bucket(a.X[i], a.nb) << 16) | (uint32_t)i) : 0xffffffffu;
-  __syncthreads();
-  if (a.nb > 0) block_bitonic_sort(keys, npow2);
-  for (uint32_t j = t; j < a.R; j += blockDim.x) {
-    const uint32_t r = keys[j] & 0xffffu;
-    a.perm[j] = r;
-    a.Xs[j] = a.X[r];
-  }
-  // boff[b] = first internal lane whose bucket is >= b
-  const uint32_t nbk = 1u << a.nb;
-  for (uint32_t b = t; b <= nbk; b += blockDim.x) {
-    uint32_t lo = 0, hi = a.R;
-    while (lo < hi) {
-      uint32_t mid = (lo + hi) >> 1;
-      if ((keys[mid] >> 16) < b) lo = mid + 1; else hi = mid;
-    }
-    a.boff[b] = lo;
-  }
-  if (t == 0 && a.keyrange) {
-    a.keyrange[0] = ~0ull;
-    a.keyrange[1] = 0ull;
-  }
+  draw_lanes(a.seed, a.R, a.nb, a.X, a.Xs, a.perm, a.boff, s_sort, a.sortbuf, a.keyrange);
 }
 
 __global__ void __launch_bounds__(512) k_prep(PrepArgs a) {
@@ -196,27 +98,6 @@ cudaError_t launch_prep(const im_workspace *ws, const QueryParams &q, bool init_
 }
 
 // ------------------------------------------------------------------ union
-struct UnionArgs {
-  const int32_t *eu, *ev;
-  int64_t m_up;
-  const uint32_t *Xs, *boff;
-  int nb;
-  uint32_t T32;
-  int all_live;
-  uint32_t R;
-  uint32_t cap;
-  int32_t *P;
-  int32_t *status;
-  // sampling options: per-edge codes (weighted), mixed hash
-  int weighted, mix;
-  const uint32_t *code_up;
-  // explicit-mask mode (test hook)
-  const uint8_t *mask;
-  const int32_t *xadj, *adj;
-};
-
-// OPTS: the sampling options (per-edge threshold codes, mixed hash) are in
-// play; the uniform-p path keeps its own instantiation.
 template <bool MASKED, bool OPTS>
 __global__ void __launch_bounds__(256) k_union(UnionArgs a) {
   extern __shared__ uint32_t s_boff[];
@@ -225,76 +106,10 @@ __global__ void __launch_bounds__(256) k_union(UnionArgs a) {
     for (int i = threadIdx.x; i <= nbk; i += blockDim.x) s_boff[i] = a.boff[i];
     __syncthreads();
   }
-  const int lane = threadIdx.x & 31;
   const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t base = gwarp * 32; base < a.m_up; base += nwarps * 32) {
-    const int64_t e = base + lane;
-    const bool valid = e < a.m_up;
-    int32_t u = 0, v = 0;
-    uint32_t h = 0, j0 = 0, c = 0, code = 0;
-    if (valid) {
-      u = a.eu[e];
-      v = a.ev[e];
-      if (MASKED) {
-        c = a.R;
-      } else if (OPTS) {
-        h = edge_hash_ordered((uint32_t)u, (uint32_t)v);
-        if (a.weighted) code = a.code_up[e];
-        uint32_t j1;
-        edge_lanes(h, a.nb, a.weighted, code, a.mix, s_boff, j0, j1);
-        c = j1 - j0;
-      } else {
-        h = edge_hash_ordered((uint32_t)u, (uint32_t)v);
-        const uint32_t b = lane_bucket(h, a.nb);
-        j0 = s_boff[b];
-        c = s_boff[b + 1] - j0;
-      }
-    }
-    // Flatten the (edge, candidate lane) pairs of the 32 edges: item k of the
-    // warp belongs to the edge whose inclusive prefix first exceeds k.
-    uint32_t incl = c;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      uint32_t t = __shfl_up_sync(kFull, incl, d);
-      if (lane >= d) incl += t;
-    }
-    const uint32_t total = __shfl_sync(kFull, incl, 31);
-    for (uint32_t k = 0; k < total; k += 32) {
-      const uint32_t item = k + lane;
-      int pos = 0;
-#pragma unroll
-      for (int step = 16; step >= 1; step >>= 1) {
-        uint32_t val = __shfl_sync(kFull, incl, pos + step - 1);
-        if (val <= item) pos += step;
-      }
-      const uint32_t s_incl = __shfl_sync(kFull, incl, pos);
-      const uint32_t s_c = __shfl_sync(kFull, c, pos);
-      const uint32_t s_j0 = __shfl_sync(kFull, j0, pos);
-      const uint32_t s_h = __shfl_sync(kFull, h, pos);
-      const int32_t s_u = __shfl_sync(kFull, u, pos);
-      const int32_t s_v = __shfl_sync(kFull, v, pos);
-      const uint32_t s_code = OPTS ? __shfl_sync(kFull, code, pos) : 0u;
-      if (item < total) {
-        const uint32_t j = s_j0 + (item - (s_incl - s_c));
-        bool live;
-        if (MASKED) {
-          int32_t lo = a.xadj[s_u], hi = a.xadj[s_u + 1];
-          while (lo < hi) {
-            int32_t mid = (lo + hi) >> 1;
-            if (a.adj[mid] < s_v) lo = mid + 1; else hi = mid;
-          }
-          live = a.mask[(uint64_t)lo * a.R + j] != 0;
-        } else if (OPTS) {
-          live = lane_live_opt(__ldg(a.Xs + j), s_h, a.T32, a.all_live, a.weighted, s_code,
-                               a.mix);
-        } else {
-          live = lane_live(__ldg(a.Xs + j), s_h, a.T32, a.all_live);
-        }
-        if (live) uf_unite(s_u, s_v, j, a.R, a.P, a.status, a.cap);
-      }
-    }
-  }
+  for (int64_t base = gwarp * 32; base < a.m_up; base += nwarps * 32)
+    union_group<MASKED, OPTS, false>(a, s_boff, base, a.m_up);
 }
 
 cudaError_t launch_union(const im_graph *g, const im_workspace *ws, const QueryParams &q,
@@ -336,103 +151,13 @@ cudaError_t launch_union(const im_graph *g, const im_workspace *ws, const QueryP
 }
 
 // ------------------------------------------------------------------ compress
-// Size memo (Section 3.3): every non-root slot gets its root (the component
-// minimum) and each root slot accumulates -|component|. The label table is
-// processed in tiles of 32 vertices x 32 lanes: the block loads a tile with
-// sector-sized row reads, then warp w takes lane j0 + w of the 32 vertices,
-// so the parent lookups of a warp hit one lane (vertices that share a parent,
-// as in a giant component, coalesce into one request) and the root counters
-// take one atomic per distinct root per warp instead of one per slot. Root
-// slots are never written here except by those atomics.
-constexpr uint32_t kCompV = 32;  // vertices per tile (one per warp lane)
-constexpr uint32_t kCompL = 32;  // lanes per tile (four per warp of the block)
-
 __global__ void __launch_bounds__(256) k_compress(int32_t *P, uint32_t n, uint32_t R,
                                                   int32_t *status, uint32_t cap) {
   __shared__ int32_t tile[kCompV][kCompL + 1];
-  const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
   const uint64_t tv = (n + kCompV - 1) / kCompV, tl = (R + kCompL - 1) / kCompL;
   const uint64_t ntiles = tv * tl;
-  const bool vec = (R & 3u) == 0;  // rows start 16-byte aligned
-  for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const uint32_t v0 = (uint32_t)(t / tl) * kCompV, j0 = (uint32_t)(t % tl) * kCompL;
-    {
-      // thread: row tid / 8, lanes 4 * (tid % 8) .. + 3 of the tile
-      const uint32_t rr = tid >> 3, c0 = (tid & 7u) * 4u;
-      const uint32_t v = v0 + rr, j = j0 + c0;
-      int32_t e[4] = {-1, -1, -1, -1};
-      if (v < n) {
-        const int32_t *row = P + (uint64_t)v * R;
-        if (vec && j + 3 < R) {
-          const int4 x4 = __ldcg(reinterpret_cast<const int4 *>(row + j));
-          e[0] = x4.x; e[1] = x4.y; e[2] = x4.z; e[3] = x4.w;
-        } else {
-#pragma unroll
-          for (int q = 0; q < 4; ++q)
-            if (j + q < R) e[q] = __ldcg(row + j + q);
-        }
-      }
-#pragma unroll
-      for (int q = 0; q < 4; ++q) tile[rr][c0 + q] = e[q];
-    }
-    __syncthreads();
-    // warp w: tile lanes w, w + 8, w + 16, w + 24 of the 32 vertices; the
-    // first parent loads of the four items are issued together
-    const uint32_t v = v0 + lane;
-    int32_t x[4], r[4];
-    bool live[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      x[q] = tile[lane][warp + 8u * q];
-      r[q] = x[q];
-      live[q] = x[q] >= 0;  // out-of-range slots were loaded as -1
-    }
-    int32_t y[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-      y[q] = live[q] ? __ldcg(P + (uint64_t)(uint32_t)r[q] * R + (j0 + warp + 8u * q)) : -1;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const uint32_t j = j0 + warp + 8u * q;
-      if (live[q] && y[q] >= 0) {  // parent is not the root: follow the chain
-        r[q] = y[q];
-        uint32_t it = 1;
-        for (; it < cap; ++it) {
-          const int32_t z = __ldcg(P + (uint64_t)(uint32_t)r[q] * R + j);
-          if (z < 0) break;
-          r[q] = z;
-        }
-        if (it == cap) {
-          set_status(status, IM_ETIMEOUT);
-          live[q] = false;
-        } else if (it > 1) {
-          // Full path compression: the chain's inner nodes (non-roots of the
-          // same component) get the root too, so later walks through them
-          // take one step. Their own slots are written with the same value
-          // when their tiles come round, so no update is lost.
-          int32_t z = x[q];  // the first parent; the walk stops at the root
-          for (uint32_t k = 0; k < it && z != r[q]; ++k) {
-            const int32_t nz = __ldcg(P + (uint64_t)(uint32_t)z * R + j);
-            if (nz < 0) break;
-            __stcg(P + (uint64_t)(uint32_t)z * R + j, r[q]);
-            z = nz;
-          }
-        }
-      }
-    }
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const uint32_t j = j0 + warp + 8u * q;
-      const uint32_t key = live[q] ? (uint32_t)r[q] : 0xffffffffu;
-      const unsigned peers = __match_any_sync(kFull, key);
-      if (live[q]) {
-        if (lane == (uint32_t)(__ffs(peers) - 1))
-          atomicAdd(P + (uint64_t)(uint32_t)r[q] * R + j, -(int32_t)__popc(peers));
-        if (r[q] != x[q]) __stcg(P + (uint64_t)v * R + j, r[q]);
-      }
-    }
-    __syncthreads();  // the tile is reloaded next iteration
-  }
+  for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x)
+    compress_tile<0>(P, n, R, status, cap, t, tile, threadIdx.x);
 }
 
 cudaError_t launch_compress(const im_graph *g, const im_workspace *ws, const QueryParams &q,

@@ -165,6 +165,34 @@ def edge_weights(xadj, adj, kind, seed):
     return vals[inv].astype(np.float64)
 
 
+def batched_instances(count=256, seed=40, n_range=(500, 200_000), Rs=(256, 1024, 2048),
+                      K_range=(5, 100), p_range=(0.001, 0.1)):
+    """Uneven independent instances for a batched launch: per instance a
+    Chung-Lu graph with n log-uniform in n_range, m/n ~ U[2, 15], exponent
+    ~ U[2, 3] and generator seed 1000 + i, and a query with p log-uniform in
+    p_range, R drawn from Rs, K ~ U{K_range} (at most n) and rng_seed 7 + i.
+    Parameters come from PCG64(seed); graphs are built lazily by `graph()`."""
+    rng = _rng(seed)
+    out = []
+    lo, hi = np.log(n_range[0]), np.log(n_range[1])
+    plo, phi = np.log(p_range[0]), np.log(p_range[1])
+    for i in range(count):
+        n = int(round(np.exp(rng.uniform(lo, hi))))
+        ratio = rng.uniform(2.0, 15.0)
+        m = min(int(round(n * ratio)), n * (n - 1) // 2)
+        gamma = rng.uniform(2.0, 3.0)
+        p = float(np.exp(rng.uniform(plo, phi)))
+        R = int(Rs[int(rng.integers(0, len(Rs)))])
+        K = int(min(rng.integers(K_range[0], K_range[1] + 1), n))
+        out.append(dict(n=n, m=m, gamma=gamma, graph_seed=1000 + i, p=p, R=R, K=K,
+                        rng_seed=7 + i))
+    return out
+
+
+def instance_graph(inst):
+    return chung_lu(inst["n"], inst["m"], inst["gamma"], inst["graph_seed"])
+
+
 # Workload recipes: graph builder, its arguments, and the query parameters.
 WORKLOADS = {
     # n=2,000 m=8,000 power-law (exponent 2.5)
