@@ -60,6 +60,12 @@ def parse_args(argv=None):
     ap.add_argument("--no-extra", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--extra-steps", type=int, default=5)
+    ap.add_argument("--batch", type=int, default=256,
+                    help="queries of the batched-launch leg (0: skip it)")
+    ap.add_argument("--batch-steps", type=int, default=5)
+    ap.add_argument("--serve", type=int, default=1000,
+                    help="queries per offered load of the serving leg (0: skip it)")
+    ap.add_argument("--serve-rates", default="50,200,1000")
     return ap.parse_args(argv)
 
 
@@ -565,6 +571,204 @@ def run_cpu_baseline(name, xadj, adj, w):
             "nproc": os.cpu_count(), "cpu": cpu_model()}
 
 
+def _instance_graph(inst):
+    from paper_2008_03095_gb300 import synth
+    return synth.instance_graph(inst)
+
+
+def batch_graphs(count):
+    """The uneven instances of the batched recipe and their graphs, built in
+    a spawn pool of host processes (started before any CUDA call)."""
+    import multiprocessing as mp
+
+    from paper_2008_03095_gb300 import synth
+    inst = synth.batched_instances(count=count)
+    procs = max(1, min(16, (os.cpu_count() or 2) - 1))
+    with mp.get_context("spawn").Pool(procs) as pool:
+        graphs = pool.map(_instance_graph, inst, chunksize=4)
+    return inst, graphs
+
+
+def serve_graphs():
+    """The serving pool's graphs: 64 of the batched recipe (parameters from
+    PCG64(50)) and the 2,000-, 15,233- and 37,154-vertex workload graphs."""
+    import multiprocessing as mp
+
+    from paper_2008_03095_gb300 import synth
+    inst = synth.batched_instances(count=64, seed=50)
+    procs = max(1, min(16, (os.cpu_count() or 2) - 1))
+    with mp.get_context("spawn").Pool(procs) as pool:
+        graphs = pool.map(_instance_graph, inst, chunksize=2)
+    for name in ("powerlaw_n2000", "powerlaw_n15233", "powerlaw_n37154"):
+        graphs.append(synth.workload_graph(name))
+    return graphs
+
+
+def run_batch(args, inst, graphs, world):
+    """The batched persistent launch of all instances against the same
+    queries one at a time (im_select_seeds_async on one stream, a workspace
+    per graph made beforehand): device time with CUDA events, W warm-up runs,
+    K timed runs each; the autotuner picks the tiling first."""
+    import torch
+
+    import paper_2008_03095_gb300 as im
+
+    dev = torch.device("cuda", dist_env()[2])
+    handles = [im.im_graph_create(x, a) for x, a in graphs]
+    queries = [dict(graph=i, K=x["K"], R=x["R"], p=x["p"], rng_seed=x["rng_seed"])
+               for i, x in enumerate(inst)]
+    units = sum(2 * x["m"] * x["R"] for x in inst)
+    stream = torch.cuda.current_stream()
+    im.im_set_stream(stream)
+    b = im.im_batch_create(handles, queries)
+    t0 = time.perf_counter()
+    im.im_batch_autotune(b, 2)
+    tune_s = time.perf_counter() - t0
+    wss = [im.im_workspace_create(h, q["R"]) for h, q in zip(handles, queries)]
+    d_seeds = [torch.empty(q["K"], dtype=torch.int32, device=dev) for q in queries]
+    d_sigma = [torch.empty(q["K"], dtype=torch.int64, device=dev) for q in queries]
+
+    def solo():
+        for i, q in enumerate(queries):
+            im.im_select_seeds_async(handles[i], wss[i], q["K"], q["R"], q["p"], q["rng_seed"],
+                                     d_seeds[i], d_sigma[i])
+
+    def timed(fn):
+        for _ in range(max(1, args.warmup // 2)):
+            fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(args.batch_steps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return ts
+
+    launches0 = im.im_kernel_launches()
+    t_batch = timed(lambda: im.im_batch_run_async(b))
+    batch_launches = (im.im_kernel_launches() - launches0) // (args.batch_steps + max(1, args.warmup // 2))
+    seeds, sigma, status = im.im_batch_results(b, check=False)
+    t_solo = timed(solo)
+    same = bool(np.all(status == 0)) and all(
+        np.array_equal(seeds[i], d_seeds[i].cpu().numpy())
+        and np.array_equal(sigma[i], d_sigma[i].cpu().numpy().astype(np.uint64))
+        for i in range(len(queries)))
+    info = im.im_batch_info(b)
+    im.im_set_stream(None)
+    for w_ in wss:
+        w_.close()
+    b.close()
+    for h in handles:
+        h.close()
+    torch.cuda.empty_cache()
+    mb, ms_ = statistics.median(t_batch), statistics.median(t_solo)
+    return {"queries": len(queries), "units": units, "n_total": int(sum(x["n"] for x in inst)),
+            "m_total": int(sum(x["m"] for x in inst)), "label_bytes": info["device_bytes"],
+            "work_items": info["items"], "launches_per_run": int(batch_launches),
+            "autotune_s": tune_s, "batch_ms": mb, "one_at_a_time_ms": ms_,
+            "value": units / (mb / 1e3) / 1e9, "value_one_at_a_time": units / (ms_ / 1e3) / 1e9,
+            "speedup": ms_ / mb, "unit": UNIT, "results_equal_one_at_a_time": same,
+            "schedule": ("query by query" if info["schedule"] else "phase by phase"),
+            "recipe": "256 Chung-Lu graphs: n log-uniform [500, 200000], m/n U[2, 15], exponent "
+                      "U[2, 3], p log-uniform [0.001, 0.1], R in {256, 1024, 2048}, K U{5..100}, "
+                      "parameters from PCG64(40), graph i seed 1000 + i"}
+
+
+def serve_queries(rng, pool_n, count):
+    """The serving recipe's query stream: 70 % select / 30 % spread of a random
+    K-subset, K ~ U{5..100} (at most n), R in {256, 1024, 2048}, p
+    log-uniform in [0.001, 0.1], over the pool's graphs uniformly."""
+    out = []
+    for _ in range(count):
+        gi = int(rng.integers(0, len(pool_n)))
+        n = pool_n[gi]
+        K = int(min(rng.integers(5, 101), n))
+        R = int(rng.choice([256, 1024, 2048]))
+        p = float(np.exp(rng.uniform(np.log(0.001), np.log(0.1))))
+        seed = int(rng.integers(0, 1 << 31))
+        if rng.random() < 0.7:
+            out.append(dict(kind=0, graph=gi, K=K, R=R, p=p, rng_seed=seed))
+        else:
+            out.append(dict(kind=1, graph=gi, K=K, R=R, p=p, rng_seed=seed,
+                            seeds=rng.choice(n, size=K, replace=False).astype(np.int32)))
+    return out
+
+
+def pct(xs, q):
+    return float(np.percentile(np.asarray(xs), q)) if len(xs) else None
+
+
+def run_serve(args, pool_graphs):
+    """Serving with continuous batching against serial execution. The pool:
+    64 graphs of the batched recipe plus the 2,000-, 15,233- and
+    37,154-vertex workload graphs, resident. For each offered load, `--serve`
+    queries arrive as a Poisson stream in real time; latency = completion -
+    arrival. Serial: the same queries' service times measured one at a time
+    (blocking calls, back to back), then queued FIFO under the same arrivals
+    (start = max(arrival, previous finish))."""
+    import paper_2008_03095_gb300 as im
+
+    handles = [im.im_graph_create(x, a) for x, a in pool_graphs]
+    pool_n = [x.shape[0] - 1 for x, _ in pool_graphs]
+    rng = np.random.default_rng(50)
+    qs = serve_queries(rng, pool_n, args.serve)
+    sv = im.im_server_create(handles, slots=16, memory_budget=160 << 30)
+
+    def submit(q):
+        return im.im_server_submit(sv, q["kind"], q["graph"], q["K"], q["R"], q["p"],
+                                   q["rng_seed"], 0, q.get("seeds"))
+
+    # warm-up: one workspace per graph at the largest R
+    for gi in range(len(handles)):
+        im.im_server_wait(sv, submit(dict(kind=0, graph=gi, K=5, R=2048, p=0.01, rng_seed=1)))
+    # serial service times
+    service = []
+    for q in qs:
+        t0 = time.perf_counter()
+        if q["kind"] == 0:
+            im.im_select_seeds(handles[q["graph"]], q["K"], q["R"], q["p"], q["rng_seed"])
+        else:
+            im.im_estimate_spread(handles[q["graph"]], q["seeds"], q["R"], q["p"], q["rng_seed"])
+        service.append(time.perf_counter() - t0)
+    out = {"queries_per_load": len(qs), "pool_graphs": len(handles), "slots": 16,
+           "serial_mean_service_ms": 1e3 * float(np.mean(service)), "loads": {}}
+    for rate in [float(r) for r in args.serve_rates.split(",")]:
+        gaps = np.random.default_rng(int(rate)).exponential(1.0 / rate, size=len(qs))
+        arrive = np.cumsum(gaps)
+        tickets = []
+        t_start = time.perf_counter()
+        for q, a in zip(qs, arrive):
+            while time.perf_counter() - t_start < a:
+                time.sleep(min(0.0005, max(0.0, a - (time.perf_counter() - t_start))))
+            tickets.append((submit(q), time.perf_counter()))
+        lat, done_t = [], []
+        for t, t_sub in tickets:
+            _, _, times = im.im_server_wait(sv, t)
+            lat.append(times[2] - times[0])
+            done_t.append(times[2])
+        span = max(done_t) - min(dt - l for dt, l in zip(done_t, lat))
+        fin, ser_lat = 0.0, []
+        for a, sv_t in zip(arrive, service):
+            fin = max(a, fin) + sv_t
+            ser_lat.append(fin - a)
+        out["loads"][str(int(rate))] = {
+            "offered_qps": rate, "p50_ms": 1e3 * pct(lat, 50), "p99_ms": 1e3 * pct(lat, 99),
+            "throughput_qps": len(qs) / span,
+            "serial_p50_ms": 1e3 * pct(ser_lat, 50), "serial_p99_ms": 1e3 * pct(ser_lat, 99),
+            "serial_throughput_qps": len(qs) / max(fin, float(arrive[-1]))}
+    st = im.im_server_stats(sv)
+    out["server_stats"] = {k: st[k] for k in ("in_flight_peak", "queue_peak", "ws_created",
+                                               "ws_evicted", "pool_bytes_peak")}
+    sv.close()
+    for h in handles:
+        h.close()
+    return out
+
+
 def run_ours(args, world):
     import torch
 
@@ -630,7 +834,13 @@ def main(argv=None):
         torch.distributed.init_process_group(
             backend="nccl" if torch.cuda.is_available() else "gloo",
             timeout=datetime.timedelta(minutes=10))
+    batch_inst = batch_graphs(args.batch) if args.batch > 0 else None
+    serve_pool = serve_graphs() if args.serve > 0 else None
     out, (xadj, adj, w, results) = run_ours(args, world)
+    if batch_inst is not None:
+        out["batched"] = run_batch(args, batch_inst[0], batch_inst[1], world)
+    if serve_pool is not None:
+        out["serving"] = run_serve(args, serve_pool)
     if world > 1:
         torch.distributed.barrier()
     if rank == 0:

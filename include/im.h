@@ -245,20 +245,86 @@ enum {
   IM_BATCH_INFO_DEVICE_BYTES = 2, /* arena size */
   IM_BATCH_INFO_TOTAL_K = 3,
   IM_BATCH_INFO_LEVELS = 4,       /* histogram of tiling levels: 4 bits per level 0..4 */
-  IM_BATCH_INFO_COUNT = 5
+  IM_BATCH_INFO_SCHEDULE = 5,     /* 0: phase by phase; 1: query by query, largest first */
+  IM_BATCH_INFO_COUNT = 6
 };
 int im_batch_info(const im_batch *b, int64_t *out);
 
 /* Autotune: for each size class (floor(log2(n*R)), R, flags) of the batch,
  * time up to four of its largest queries as a batch of their own at each of
  * five tiling granularities (trials timed runs each, after a warm-up) and keep
- * the fastest in a process-wide cache; then re-plan b with it. Later batches
- * of the same classes use the cache. The cache can be saved to and loaded
- * from a text file. */
+ * the fastest in a process-wide cache; then time b's two item orders (phase by
+ * phase, or query by query with the largest first) and keep the faster for b.
+ * Later batches of the same classes use the cache. The cache can be saved to
+ * and loaded from a text file. */
 int im_batch_autotune(im_batch *b, int32_t trials);
 int im_autotune_cache_save(const char *path);
 int im_autotune_cache_load(const char *path);
 int im_autotune_cache_clear(void);
+
+/* ---------------------------------------------------------------- serving
+ * A serving loop over a resident pool of graphs: influence queries arrive at
+ * any time (any thread) and a scheduler thread of the library admits them in
+ * arrival order as soon as one of `slots` CUDA streams is free and the
+ * query's workspace fits the memory budget (workspaces are pooled per graph
+ * and reused; idle ones are freed least recently used first when a new one
+ * would exceed the budget). Queries that arrive while others are on the GPU
+ * are admitted into the running mix and their kernels overlap on the device
+ * (continuous batching, not a queue in front of one query at a time). Each
+ * query runs exactly the kernels of its blocking call, so its result is the
+ * same alone and in the mix. This is an interface of this library; the paper
+ * has none (it runs one query at a time). */
+typedef struct im_server im_server; /* opaque, library-owned */
+enum { IM_REQUEST_SELECT = 0, IM_REQUEST_SPREAD = 1 };
+typedef struct {
+  int32_t kind;          /* IM_REQUEST_SELECT or IM_REQUEST_SPREAD */
+  int32_t graph;         /* index into the server's graphs */
+  int32_t K;             /* select: seeds to choose (1..n); spread: seeds given (0..n) */
+  int32_t R;
+  double p;
+  uint32_t rng_seed;
+  uint32_t flags;        /* IM_SAMPLE_* */
+  const int32_t *seeds;  /* spread: K host ids, copied at submission */
+} im_request;
+
+/* graphs: num_graphs handles on one device, which must outlive the server.
+ * slots: queries on the GPU at once (1..256); memory_budget: bytes of device
+ * memory the pooled workspaces may take. Starts the scheduler thread. */
+int im_server_create(const im_graph *const *graphs, int32_t num_graphs, int32_t slots,
+                     int64_t memory_budget, im_server **out);
+
+/* Queue a query; *ticket identifies it. Thread-safe. Errors: IM_EINVAL (bad
+ * query), IM_ENOMEM (its workspace alone exceeds the budget), IM_EBUSY
+ * (server shutting down). */
+int im_server_submit(im_server *s, const im_request *r, uint64_t *ticket);
+
+/* Wait up to timeout_us (0: just poll, < 0: until done) for a query. Done:
+ * select writes out_seeds[K] and out_sigma_R[K] (cumulative), spread writes
+ * out_sigma_R[0]; out_times (may be NULL) gets the seconds since server
+ * creation at submission, admission and completion; the ticket is released
+ * and the query's own status returned. Not done: IM_EBUSY, ticket kept. */
+int im_server_wait(im_server *s, uint64_t ticket, int64_t timeout_us, int32_t *out_seeds,
+                   uint64_t *out_sigma_R, double *out_times);
+
+enum {
+  IM_SERVER_STAT_SUBMITTED = 0,
+  IM_SERVER_STAT_ADMITTED = 1,
+  IM_SERVER_STAT_COMPLETED = 2,
+  IM_SERVER_STAT_IN_FLIGHT = 3,
+  IM_SERVER_STAT_IN_FLIGHT_PEAK = 4,
+  IM_SERVER_STAT_QUEUED = 5,
+  IM_SERVER_STAT_QUEUE_PEAK = 6,
+  IM_SERVER_STAT_WS_CREATED = 7,
+  IM_SERVER_STAT_WS_EVICTED = 8,
+  IM_SERVER_STAT_POOL_BYTES = 9,
+  IM_SERVER_STAT_POOL_BYTES_PEAK = 10,
+  IM_SERVER_STAT_BUDGET = 11,
+  IM_SERVER_STAT_COUNT = 12
+};
+int im_server_stats(im_server *s, int64_t *out);
+
+/* Finish every queued and running query, then free the server. */
+int im_server_destroy(im_server *s);
 
 /* Synchronize the thread's stream and return (then clear) the first device
  * status recorded in ws since the last call: IM_OK, IM_EINVAL, IM_ETIMEOUT or

@@ -18,7 +18,9 @@ from ._binding import (IM_EBUSY, IM_ECUDA, IM_EINTERNAL, IM_EINVAL, IM_ENOMEM, I
                        im_batch_create, im_batch_run_async, im_batch_results,
                        im_batch_query_stats, im_batch_info, im_batch_autotune,
                        im_batch_destroy, im_autotune_cache_save, im_autotune_cache_load,
-                       im_autotune_cache_clear, BATCH_INFO,
+                       im_autotune_cache_clear, BATCH_INFO, Server, Request,
+                       IM_REQUEST_SELECT, IM_REQUEST_SPREAD, im_server_create, im_server_submit,
+                       im_server_wait, im_server_stats, im_server_destroy, SERVER_STATS,
                        im_estimate_spread, im_estimate_spread_async, im_estimate_spread_noalloc,
                        im_graph_create, NOALLOC_LIMITS,
                        im_graph_create_raw, im_graph_destroy, im_graph_info, im_kernel_launches,

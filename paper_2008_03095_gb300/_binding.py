@@ -85,6 +85,11 @@ def lib():
         "im_autotune_cache_save": [ctypes.c_char_p],
         "im_autotune_cache_load": [ctypes.c_char_p],
         "im_autotune_cache_clear": [],
+        "im_server_create": [P, i32, i32, i64, P],
+        "im_server_submit": [P, P, P],
+        "im_server_wait": [P, u64, i64, P, P, P],
+        "im_server_stats": [P, P],
+        "im_server_destroy": [P],
         "im_debug_tables_ex": [P, i32, f64, u32, u32, P, P],
         "im_select_seeds_ex": [P, i32, i32, f64, u32, u32, P, P],
         "im_estimate_spread_ex": [P, P, i32, i32, f64, u32, u32, P],
@@ -520,7 +525,7 @@ def im_batch_query_stats(b, query):
     return {name: int(out[i]) for i, name in enumerate(STATS)}
 
 
-BATCH_INFO = ("queries", "items", "device_bytes", "total_K", "levels")
+BATCH_INFO = ("queries", "items", "device_bytes", "total_K", "levels", "schedule")
 
 
 def im_batch_info(b):
@@ -547,3 +552,91 @@ def im_autotune_cache_load(path):
 
 def im_autotune_cache_clear():
     _check(lib().im_autotune_cache_clear())
+
+
+# ------------------------------------------------------------------ serving
+
+IM_REQUEST_SELECT = 0
+IM_REQUEST_SPREAD = 1
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("graph", ctypes.c_int32), ("K", ctypes.c_int32),
+                ("R", ctypes.c_int32), ("p", ctypes.c_double), ("rng_seed", ctypes.c_uint32),
+                ("flags", ctypes.c_uint32), ("seeds", ctypes.c_void_p)]
+
+
+class Server:
+    """Owning wrapper of an im_server handle; keeps its graphs alive."""
+
+    def __init__(self, handle, graphs):
+        self.handle = handle
+        self.graphs = graphs
+        self.kinds = {}
+
+    def close(self):
+        if self.handle:
+            _check(lib().im_server_destroy(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def im_server_create(graphs, slots=8, memory_budget=64 << 30):
+    handles = (ctypes.c_void_p * len(graphs))(*[_gh(g).value if hasattr(_gh(g), "value")
+                                                else _gh(g) for g in graphs])
+    out = ctypes.c_void_p()
+    _check(lib().im_server_create(handles, len(graphs), slots, int(memory_budget),
+                                  ctypes.byref(out)))
+    return Server(out, list(graphs))
+
+
+def im_server_submit(sv, kind, graph, K, R, p, rng_seed, flags=0, seeds=None):
+    """Queue a query; returns its ticket. spread: seeds is the seed set (K = len)."""
+    arr = None
+    if kind == IM_REQUEST_SPREAD:
+        arr = np.ascontiguousarray(seeds if seeds is not None else [], dtype=np.int32)
+        K = arr.shape[0]
+    req = Request(kind, graph, K, R, float(p), rng_seed & 0xFFFFFFFF, flags,
+                  arr.ctypes.data if arr is not None and arr.size else None)
+    t = ctypes.c_uint64()
+    _check(lib().im_server_submit(sv.handle, ctypes.byref(req), ctypes.byref(t)))
+    sv.kinds[t.value] = (kind, K)
+    return t.value
+
+
+def im_server_wait(sv, ticket, timeout_us=-1):
+    """select: (seeds, sigma, times); spread: (None, sigmaR, times). times =
+    (submitted, admitted, done) in seconds since the server started. Raises
+    IMError(IM_EBUSY) if not done within timeout_us (0 = poll)."""
+    kind, K = sv.kinds[ticket]
+    seeds = np.empty(max(K, 1), dtype=np.int32)
+    sigma = np.empty(max(K, 1), dtype=np.uint64)
+    times = np.zeros(3, dtype=np.float64)
+    rc = lib().im_server_wait(sv.handle, ticket, int(timeout_us), _ptr(seeds), _ptr(sigma),
+                              _ptr(times))
+    if rc != IM_EBUSY:
+        sv.kinds.pop(ticket, None)
+    _check(rc)
+    if kind == IM_REQUEST_SELECT:
+        return seeds[:K], sigma[:K], tuple(times)
+    return None, int(sigma[0]), tuple(times)
+
+
+SERVER_STATS = ("submitted", "admitted", "completed", "in_flight", "in_flight_peak", "queued",
+                "queue_peak", "ws_created", "ws_evicted", "pool_bytes", "pool_bytes_peak",
+                "budget")
+
+
+def im_server_stats(sv):
+    out = np.zeros(len(SERVER_STATS), dtype=np.int64)
+    _check(lib().im_server_stats(sv.handle, _ptr(out)))
+    return {name: int(out[i]) for i, name in enumerate(SERVER_STATS)}
+
+
+def im_server_destroy(sv):
+    sv.close()

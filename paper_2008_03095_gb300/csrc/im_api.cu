@@ -385,35 +385,6 @@ int ensure_seed_in(im_workspace *ws, int64_t count) {
   return IM_OK;
 }
 
-}  // namespace
-
-namespace imgb {
-
-int api_error(int code, const char *fmt, ...) {
-  char buf[512];
-  va_list ap;
-  va_start(ap, fmt);
-  std::vsnprintf(buf, sizeof(buf), fmt, ap);
-  va_end(ap);
-  t_err = buf;
-  return code;
-}
-
-int api_cuda_error(cudaError_t e, const char *what) { return cuda_fail(e, what); }
-
-cudaStream_t api_stream() { return t_stream; }
-
-void api_count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
-
-int api_query_params(const im_graph *g, int32_t R, double p, uint32_t seed, uint32_t flags,
-                     QueryParams *q) {
-  return make_params_ex(g, R, p, seed, flags, q);
-}
-
-}  // namespace imgb
-
-namespace {
-
 // FusedSampling (Section 4, Table 4): MixGreedy with the paper's fused hash
 // sampling but none of its batching or memoization. Simulation r runs alone
 // on a one-lane view of the workspace (its X_r, one lane bucket): the
@@ -553,6 +524,70 @@ int fused_sampling_select(im_graph *g, im_workspace *ws, int32_t K, const QueryP
 }
 
 }  // namespace
+
+namespace imgb {
+
+int api_error(int code, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  std::vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  t_err = buf;
+  return code;
+}
+
+int api_cuda_error(cudaError_t e, const char *what) { return cuda_fail(e, what); }
+
+cudaStream_t api_stream() { return t_stream; }
+
+void api_count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+int api_query_params(const im_graph *g, int32_t R, double p, uint32_t seed, uint32_t flags,
+                     QueryParams *q) {
+  return make_params_ex(g, R, p, seed, flags, q);
+}
+
+int api_ws_create(const im_graph *g, int32_t R_max, im_workspace **out) {
+  return ws_create(g, R_max, out);
+}
+
+void api_ws_destroy(im_workspace *ws) {
+  ws_free(ws);
+  delete ws;
+}
+
+// Mirrors ws_create's allocations (each rounded up to the allocator's 512 B).
+size_t api_ws_bytes(const im_graph *g, int32_t R_max) {
+  const size_t n = (size_t)g->n, nR = n * (size_t)R_max, W = ((size_t)R_max + 31) / 32;
+  size_t npow2 = 1;
+  while (npow2 < (size_t)R_max) npow2 <<= 1;
+  const size_t q = n + (size_t)g->m / 16 + 1;
+  const size_t parts[] = {4 * nR, 4 * ((nR + 31) / 32), 8 * n, 16, n, celf_ctl_bytes(),
+                          (size_t)R_max * 8 > (size_t)160 * 1024 ? 4 * 2 * 8 * (size_t)R_max : 4,
+                          4 * (size_t)R_max, 4 * (size_t)R_max, 4 * (size_t)R_max,
+                          4 * ((1u << kMaxBucketBits) + 1),
+                          npow2 > (size_t)kSortSmemMax ? 4 * npow2 : 4, 4 * n * W, 4 * n * W,
+                          4 * n * W, 4 * n * W, 4 * n, 4 * n, 4 * n, 8 * q, 8 * q, 8 * q, 4 * n,
+                          8 * (n + 4), 8, 8 * IM_NUM_STATS, 4, 4 * n, 8 * n};
+  size_t b = 0;
+  for (size_t x : parts) b += (x + 511) & ~(size_t)511;
+  return b;
+}
+
+int api_ws_seed_capacity(im_workspace *ws, int64_t count) { return ensure_seed_in(ws, count); }
+
+int api_enqueue_select(const im_graph *g, const im_workspace *ws, int32_t K, const QueryParams &q,
+                       int32_t *d_seeds, uint64_t *d_sigma, cudaStream_t s) {
+  return enqueue_select(g, ws, K, q, nullptr, d_seeds, d_sigma, s, false);
+}
+
+int api_enqueue_spread(const im_graph *g, const im_workspace *ws, const int32_t *d_seeds,
+                       int32_t ns, const QueryParams &q, uint64_t *d_sigma, cudaStream_t s) {
+  return enqueue_spread(g, ws, d_seeds, ns, q, nullptr, d_sigma, s);
+}
+
+}  // namespace imgb
 
 namespace {
 

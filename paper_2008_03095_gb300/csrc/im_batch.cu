@@ -476,6 +476,7 @@ struct im_batch {
   std::vector<im_batch_query> query;
   std::vector<QueryParams> params;
   std::vector<int> level;                // tiling level per query
+  int schedule = 0;                      // 0: phase by phase; 1: query by query, largest first
   std::vector<int64_t> seed_off;         // prefix sums of K
   int64_t total_K = 0;
   void *arena = nullptr;                 // every per-query table, one allocation
@@ -494,8 +495,12 @@ struct im_batch {
 
 namespace {
 
-// Item lists of the batch for its queries' current tiling levels: phase by
-// phase, each phase's queries largest first.
+// Item lists of the batch for its queries' current tiling levels, in one of
+// two orders (the schedule): phase by phase (each phase's queries largest
+// first), or query by query, largest first, every phase of a query before the
+// next query's -- the largest queries' lazy greedies then start early and
+// overlap the other queries' bandwidth phases instead of forming the tail.
+// Either order puts every item after the items it depends on.
 int batch_plan(im_batch *b) {
   std::vector<int32_t> order(b->count);
   for (int32_t i = 0; i < b->count; ++i) order[i] = i;
@@ -522,10 +527,17 @@ int batch_plan(im_batch *b) {
     I.items[kPhGains] = (uint32_t)((I.n + t.gains_chunk - 1) / t.gains_chunk);
     I.items[kPhCelf] = I.K > 0 ? 1u : 0u;
   }
-  for (uint32_t ph = 0; ph < kNumPhases; ++ph)
+  if (b->schedule == 0) {
+    for (uint32_t ph = 0; ph < kNumPhases; ++ph)
+      for (int32_t i : order)
+        for (uint32_t k = 0; k < b->h_inst[i].items[ph]; ++k)
+          items.push_back(((uint64_t)i << 44) | ((uint64_t)ph << 40) | k);
+  } else {
     for (int32_t i : order)
-      for (uint32_t k = 0; k < b->h_inst[i].items[ph]; ++k)
-        items.push_back(((uint64_t)i << 44) | ((uint64_t)ph << 40) | k);
+      for (uint32_t ph = 0; ph < kNumPhases; ++ph)
+        for (uint32_t k = 0; k < b->h_inst[i].items[ph]; ++k)
+          items.push_back(((uint64_t)i << 44) | ((uint64_t)ph << 40) | k);
+  }
   if (items.size() >= (1ull << 32)) return api_error(IM_EINVAL, "batch has too many work items");
   cudaError_t e = cudaSuccess;
   if (items.size() > b->items_cap) {
@@ -791,6 +803,7 @@ int im_batch_info(const im_batch *b, int64_t *out) {
   int64_t hist = 0;
   for (int32_t i = 0; i < b->count; ++i) hist += (int64_t)1 << (4 * b->level[i]);
   out[IM_BATCH_INFO_LEVELS] = hist;
+  out[IM_BATCH_INFO_SCHEDULE] = b->schedule;
   return IM_OK;
 }
 
@@ -857,14 +870,38 @@ int im_batch_autotune(im_batch *b, int32_t trials) {
     std::lock_guard<std::mutex> lock(g_tune_mu);
     g_tune[kv.first] = best;
   }
+  if (rc == IM_OK) {
+    for (int32_t i = 0; i < b->count; ++i) {
+      const int lv = tuned_level(tune_key((uint32_t)b->graph[i]->n, (uint32_t)b->query[i].R,
+                                          b->query[i].flags));
+      if (lv >= 0) b->level[i] = lv;
+    }
+    // the schedule: both orders on the whole batch, the faster kept
+    float sched_ms[2] = {0.f, 0.f};
+    for (int sc = 0; sc < 2 && rc == IM_OK; ++sc) {
+      b->schedule = sc;
+      rc = batch_plan(b);
+      std::vector<float> ms;
+      for (int r = 0; r <= trials && rc == IM_OK; ++r) {
+        cudaEventRecord(e0, s);
+        rc = batch_enqueue(b, s);
+        cudaEventRecord(e1, s);
+        if (rc == IM_OK && cudaEventSynchronize(e1) != cudaSuccess)
+          rc = api_error(IM_ECUDA, "autotune timing");
+        float x = 0.f;
+        cudaEventElapsedTime(&x, e0, e1);
+        if (r > 0) ms.push_back(x);
+      }
+      if (rc == IM_OK) {
+        std::sort(ms.begin(), ms.end());
+        sched_ms[sc] = ms[ms.size() / 2];
+      }
+    }
+    if (rc == IM_OK) b->schedule = sched_ms[1] < sched_ms[0] ? 1 : 0;
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rc != IM_OK) return rc;
-  for (int32_t i = 0; i < b->count; ++i) {
-    const int lv = tuned_level(tune_key((uint32_t)b->graph[i]->n, (uint32_t)b->query[i].R,
-                                        b->query[i].flags));
-    if (lv >= 0) b->level[i] = lv;
-  }
   return batch_plan(b);
 }
 

@@ -274,6 +274,15 @@ void api_count_launch();                                  // one more kernel in 
 // Query parameters of R, p, rng_seed under the IM_SAMPLE_* flags (IM_EINVAL on bad input).
 int api_query_params(const im_graph *g, int32_t R, double p, uint32_t seed, uint32_t flags,
                      QueryParams *q);
+// Workspaces and the kernel sequences of one query (queued on s, no sync).
+int api_ws_create(const im_graph *g, int32_t R_max, im_workspace **out);
+void api_ws_destroy(im_workspace *ws);
+size_t api_ws_bytes(const im_graph *g, int32_t R_max);  // device bytes of a workspace
+int api_ws_seed_capacity(im_workspace *ws, int64_t count);
+int api_enqueue_select(const im_graph *g, const im_workspace *ws, int32_t K, const QueryParams &q,
+                       int32_t *d_seeds, uint64_t *d_sigma, cudaStream_t s);
+int api_enqueue_spread(const im_graph *g, const im_workspace *ws, const int32_t *d_seeds,
+                       int32_t ns, const QueryParams &q, uint64_t *d_sigma, cudaStream_t s);
 
 // ------------------------------------------------------------------ launchers
 // All launchers queue work on `s` and return the launch error (if any).
