@@ -652,6 +652,14 @@ def run_batch(args, inst, graphs, world):
     t_batch = timed(lambda: im.im_batch_run_async(b))
     batch_launches = (im.im_kernel_launches() - launches0) // (args.batch_steps + max(1, args.warmup // 2))
     seeds, sigma, status = im.im_batch_results(b, check=False)
+    # the lazy-greedy items (one SM each): whole item and bound refreshes, in
+    # SM cycles (converted at the 2070 MHz the bench runs at)
+    item_cyc, ref_cyc = [], []
+    for i in range(len(queries)):
+        st = im.im_batch_query_stats(b, i)
+        item_cyc.append(st["celf_cycles_eval"])
+        ref_cyc.append(st["celf_cycles_refresh"])
+    slowest = int(np.argmax(item_cyc))
     t_solo = timed(solo)
     same = bool(np.all(status == 0)) and all(
         np.array_equal(seeds[i], d_seeds[i].cpu().numpy())
@@ -673,6 +681,10 @@ def run_batch(args, inst, graphs, world):
             "value": units / (mb / 1e3) / 1e9, "value_one_at_a_time": units / (ms_ / 1e3) / 1e9,
             "speedup": ms_ / mb, "unit": UNIT, "results_equal_one_at_a_time": same,
             "schedule": ("query by query" if info["schedule"] else "phase by phase"),
+            "slowest_celf_item_ms": item_cyc[slowest] / 2.07e6,
+            "slowest_celf_item_refresh_ms": ref_cyc[slowest] / 2.07e6,
+            "slowest_celf_item_query": {k: inst[slowest][k] for k in ("n", "m", "R", "K", "p")},
+            "celf_items_ms_sum": sum(item_cyc) / 2.07e6,
             "recipe": "256 Chung-Lu graphs: n log-uniform [500, 200000], m/n U[2, 15], exponent "
                       "U[2, 3], p log-uniform [0.001, 0.1], R in {256, 1024, 2048}, K U{5..100}, "
                       "parameters from PCG64(40), graph i seed 1000 + i"}

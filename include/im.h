@@ -346,7 +346,8 @@ enum {
   IM_STAT_CELF_CYC_COMMITS = 9,  /* ... in the commit loop (picks, pool updates) */
   IM_STAT_CELF_CYC_COVER = 10,   /* ... marking committed components covered */
   IM_STAT_CELF_REFRESHED = 11,   /* vertices re-evaluated by the refreshes */
-  IM_STAT_RESERVED_12 = 12,      /* 0 */
+  IM_STAT_CELF_CYC_REFRESH = 12, /* batched lazy greedy: SM cycles in bound refreshes (a batch
+                                    query's IM_STAT_CELF_CYC_EVAL holds its whole item) */
   IM_STAT_CHECK_CODE = 13,       /* first failed internal invariant check (0 = none) */
   IM_STAT_CHECK_V0 = 14,         /* ... and two values describing it */
   IM_STAT_CHECK_V1 = 15,

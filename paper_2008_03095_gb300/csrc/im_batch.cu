@@ -269,17 +269,21 @@ __device__ void batch_celf(const BatchInst &I, CelfSmem &s, uint32_t *dyn) {
   uint32_t *pcont = proot + (size_t)a.B * a.R;
   for (uint32_t i = tid; i < a.n; i += blockDim.x) a.chosen[i] = 0;
   __syncthreads();
+  const long long t_item = clock64();
   Driver d;
   bool bounded = false;
   uint64_t hi = 0;
   uint64_t A0 = __ldcg(I.keyrange), B0 = __ldcg(I.keyrange + 1);
+  unsigned long long cyc_refresh = 0;
   uint32_t extracts = 0, refreshes = 0;
   int cmd = kCmdExtract;
   uint32_t outer = 0;
   for (; outer < a.round_cap; ++outer) {
     const long long t0 = clock64();
     if (cmd == kCmdRefresh) {
+      const long long tr = clock64();
       block_refresh(a, d.lb, s, A0, B0);
+      cyc_refresh += (unsigned long long)(clock64() - tr);
       bounded = false;
       hi = 0;
       ++refreshes;
@@ -330,6 +334,11 @@ __device__ void batch_celf(const BatchInst &I, CelfSmem &s, uint32_t *dyn) {
     atomicAdd(a.stats + 1, (unsigned long long)d.evals);
     atomicAdd(a.stats + 2, (unsigned long long)extracts);
     atomicAdd(a.stats + 8, (unsigned long long)refreshes);
+    // SM cycles: 4 = prefix extraction (with refreshes), 5 = the whole item,
+    // 12 = refreshes alone
+    atomicAdd(a.stats + 4, d.cyc[0]);
+    atomicAdd(a.stats + 5, (unsigned long long)(clock64() - t_item));
+    atomicAdd(a.stats + 12, cyc_refresh);
   }
 }
 

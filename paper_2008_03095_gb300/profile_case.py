@@ -23,6 +23,11 @@ def main(argv=None):
     ap.add_argument("--p", type=float, default=None)
     ap.add_argument("--repeat", type=int, default=2)
     ap.add_argument("--no-spread", action="store_true")
+    ap.add_argument("--spread-only", action="store_true",
+                    help="run only the spread, from an async workspace")
+    ap.add_argument("--chung-lu", default=None,
+                    help="n,m,gamma,seed: a Chung-Lu graph instead of a named workload")
+    ap.add_argument("--R", type=int, default=None)
     args = ap.parse_args(argv)
 
     sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
@@ -32,21 +37,41 @@ def main(argv=None):
     from paper_2008_03095_gb300 import build, synth
 
     build.build()
-    w = synth.WORKLOADS[args.workload]
+    if args.chung_lu:
+        n_, m_, gamma_, gseed = args.chung_lu.split(",")
+        xadj, adj = synth.chung_lu(int(n_), int(m_), float(gamma_), int(gseed))
+        w = dict(R=512, K=50, rng_seed=7, ps=(0.01,))
+        args.workload = "chung_lu(%s)" % args.chung_lu
+    else:
+        w = synth.WORKLOADS[args.workload]
+        xadj, adj = synth.workload_graph(args.workload)
     p = w["ps"][-1] if args.p is None else args.p
-    R, K, seed = w["R"], w["K"], w["rng_seed"]
-    xadj, adj = synth.workload_graph(args.workload)
+    R = w["R"] if args.R is None else args.R
+    K, seed = w["K"], w["rng_seed"]
     deg = np.diff(xadj)
     seeds = np.argsort(-deg, kind="stable")[:K].astype(np.int32)
     torch.cuda.set_device(0)
     g = im.im_graph_create(xadj, adj)
+    mg = np.zeros(1, dtype=np.uint64)
+    if args.spread_only:
+        ws = im.im_workspace_create(g, R)
+        d_seeds = torch.from_numpy(seeds).cuda()
+        d_sigma = torch.empty(1, dtype=torch.int64, device="cuda")
+        im.im_set_stream(torch.cuda.current_stream())
     im.im_profile_enable(True)
     for _ in range(args.repeat):
+        if args.spread_only:
+            im.im_estimate_spread_async(g, ws, d_seeds, K, R, p, seed, d_sigma)
+            continue
         mg = im.im_debug_first_gains(g, R, p, seed)
         if not args.no_spread:
             im.im_estimate_spread(g, seeds, R, p, seed)
     prof = im.im_profile_read()
     im.im_profile_enable(False)
+    if args.spread_only:
+        im.im_workspace_status(ws)
+        ws.close()
+        im.im_set_stream(None)
     g.close()
     print(json.dumps({"workload": args.workload, "p": p, "R": R, "repeat": args.repeat,
                       "max_first_gain": int(mg.max()),
