@@ -660,6 +660,7 @@ def run_batch(args, inst, graphs, world):
         item_cyc.append(st["celf_cycles_eval"])
         ref_cyc.append(st["celf_cycles_refresh"])
     slowest = int(np.argmax(item_cyc))
+    cyc = im.im_batch_phase_cycles(b)  # of the last timed run
     t_solo = timed(solo)
     same = bool(np.all(status == 0)) and all(
         np.array_equal(seeds[i], d_seeds[i].cpu().numpy())
@@ -680,11 +681,14 @@ def run_batch(args, inst, graphs, world):
             "autotune_s": tune_s, "batch_ms": mb, "one_at_a_time_ms": ms_,
             "value": units / (mb / 1e3) / 1e9, "value_one_at_a_time": units / (ms_ / 1e3) / 1e9,
             "speedup": ms_ / mb, "unit": UNIT, "results_equal_one_at_a_time": same,
-            "schedule": ("query by query" if info["schedule"] else "phase by phase"),
+            "schedule_group": info["schedule"],
             "slowest_celf_item_ms": item_cyc[slowest] / 2.07e6,
             "slowest_celf_item_refresh_ms": ref_cyc[slowest] / 2.07e6,
             "slowest_celf_item_query": {k: inst[slowest][k] for k in ("n", "m", "R", "K", "p")},
             "celf_items_ms_sum": sum(item_cyc) / 2.07e6,
+            "sm_ms_per_phase": {"work": {k: v / 2.07e6 for k, v in cyc["work"].items()},
+                                "wait": {k: v / 2.07e6 for k, v in cyc["wait"].items()},
+                                "help": cyc["help"] / 2.07e6},
             "recipe": "256 Chung-Lu graphs: n log-uniform [500, 200000], m/n U[2, 15], exponent "
                       "U[2, 3], p log-uniform [0.001, 0.1], R in {256, 1024, 2048}, K U{5..100}, "
                       "parameters from PCG64(40), graph i seed 1000 + i"}

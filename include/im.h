@@ -64,7 +64,11 @@ typedef struct im_workspace im_workspace; /* opaque, library-owned */
 
 /* ---------------------------------------------------------------- graphs */
 
-/* Validate a symmetric CSR (host arrays, see Conventions) and copy it to the
+/* The influence graph G = (V, E) of the problem statement (Section 2.1),
+ * undirected, held in the CSR form every algorithm of the paper reads
+ * (Section 3.4, implementation details: xadj[v] is where v's neighbours
+ * start in adj; every undirected edge appears as two arcs).
+ * Validate a symmetric CSR (host arrays, see Conventions) and copy it to the
  * current device, where it stays resident until im_graph_destroy. The
  * library also derives the upper-triangle edge list {u < v} used by the
  * component kernel. Blocking. The caller keeps ownership of xadj/adj.
@@ -86,7 +90,9 @@ int im_graph_create(int32_t n, int64_t m, const int32_t *xadj, const int32_t *ad
 int im_graph_create_weighted(int32_t n, int64_t m, const int32_t *xadj, const int32_t *adj,
                              const double *w, im_graph **out);
 
-/* Release a graph and its device memory (and its internal workspace). */
+/* Release a graph of Section 2.1 and its device memory (its CSR copy, edge
+ * list, weight codes and internal workspace). Workspaces, batches and
+ * servers built on it must be destroyed first. Errors: IM_EINVAL (null). */
 int im_graph_destroy(im_graph *g);
 
 /* Number of vertices and undirected edges (m = len(adj) / 2). */
@@ -225,8 +231,10 @@ int im_batch_create(const im_graph *const *graphs, int32_t num_graphs,
                     const im_batch_query *queries, int32_t count, im_batch **out);
 int im_batch_destroy(im_batch *b);
 
-/* Queue one run of all queries on the thread's stream: three small resets
- * and one persistent launch of one 1024-thread block per SM. Runs may repeat;
+/* Queue one run of all queries on the thread's stream: four small resets
+ * and one persistent launch of one 1024-thread block per SM. A query's large
+ * bound refreshes are cut into chunks that blocks without other work claim,
+ * so the largest lazy greedies do not run on one SM alone. Runs may repeat;
  * each overwrites the results. */
 int im_batch_run_async(im_batch *b);
 
@@ -245,16 +253,24 @@ enum {
   IM_BATCH_INFO_DEVICE_BYTES = 2, /* arena size */
   IM_BATCH_INFO_TOTAL_K = 3,
   IM_BATCH_INFO_LEVELS = 4,       /* histogram of tiling levels: 4 bits per level 0..4 */
-  IM_BATCH_INFO_SCHEDULE = 5,     /* 0: phase by phase; 1: query by query, largest first */
+  IM_BATCH_INFO_SCHEDULE = 5,     /* queries per schedule group (1: query by query; all: phase
+                                     by phase) */
   IM_BATCH_INFO_COUNT = 6
 };
 int im_batch_info(const im_batch *b, int64_t *out);
 
+/* SM cycles of the last run, summed over blocks: out[0..5] waiting for
+ * dependencies and out[6..11] working, for the phases lanes, init, union,
+ * compress, gains, lazy greedy; out[12] refresh chunks done for other
+ * queries' lazy greedies. 13 int64 values. */
+int im_batch_phase_cycles(im_batch *b, int64_t *out);
+
 /* Autotune: for each size class (floor(log2(n*R)), R, flags) of the batch,
  * time up to four of its largest queries as a batch of their own at each of
  * five tiling granularities (trials timed runs each, after a warm-up) and keep
- * the fastest in a process-wide cache; then time b's two item orders (phase by
- * phase, or query by query with the largest first) and keep the faster for b.
+ * the fastest in a process-wide cache; then time b's item orders (queries,
+ * largest first, in groups of 1, 2, 4, 8, 16, 32, 64 or all, each group phase
+ * by phase) and keep the fastest for b.
  * Later batches of the same classes use the cache. The cache can be saved to
  * and loaded from a text file. */
 int im_batch_autotune(im_batch *b, int32_t trials);
@@ -463,7 +479,8 @@ enum {
                                   device were out of memory (1 = the next one); one shot */
   IM_OVR_CELF_REFRESH_AFTER = 5, /* lazy greedy: exact evaluations without a commit before all
                                     gains are recomputed (any value keeps the result exact) */
-  IM_NUM_OVERRIDES = 6
+  IM_OVR_BATCH_GROUP = 6,        /* batches planned from now: queries per schedule group */
+  IM_NUM_OVERRIDES = 7
 };
 /* Errors: IM_EINVAL (unknown key, or a value outside the key's range). */
 int im_debug_override(int32_t key, int64_t value);

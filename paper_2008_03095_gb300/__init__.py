@@ -10,14 +10,14 @@ from ._binding import (IM_EBUSY, IM_ECUDA, IM_EINTERNAL, IM_EINVAL, IM_ENOMEM, I
                        im_debug_lane_randoms, im_debug_select_seeds_masked, im_debug_sizes,
                        im_debug_tables_lanes, im_debug_override, im_debug_clear_overrides, im_debug_first_gains,
                        IM_OVR_CELF_CLUSTER, IM_OVR_CELF_ROUND_CAP, IM_OVR_UF_CAP,
-                       IM_OVR_SPREAD_LEVEL_CAP, IM_OVR_FAIL_ALLOC, IM_OVR_CELF_REFRESH_AFTER,
+                       IM_OVR_SPREAD_LEVEL_CAP, IM_OVR_FAIL_ALLOC, IM_OVR_CELF_REFRESH_AFTER, IM_OVR_BATCH_GROUP,
                        IM_NUM_OVERRIDES, IM_SAMPLE_EDGE_WEIGHTS, IM_SAMPLE_MIXED_HASH,
                        IM_ALGO_FUSED_SAMPLING, im_graph_create_weighted, im_select_seeds_ex,
                        im_estimate_spread_ex, im_select_seeds_ex_async,
                        im_estimate_spread_ex_async, im_debug_tables_ex, Batch, BatchQuery,
                        im_batch_create, im_batch_run_async, im_batch_results,
                        im_batch_query_stats, im_batch_info, im_batch_autotune,
-                       im_batch_destroy, im_autotune_cache_save, im_autotune_cache_load,
+                       im_batch_destroy, im_batch_phase_cycles, BATCH_PHASES, im_autotune_cache_save, im_autotune_cache_load,
                        im_autotune_cache_clear, BATCH_INFO, Server, Request,
                        IM_REQUEST_SELECT, IM_REQUEST_SPREAD, im_server_create, im_server_submit,
                        im_server_wait, im_server_stats, im_server_destroy, SERVER_STATS,

@@ -81,6 +81,7 @@ def lib():
         "im_batch_results": [P, P, P, P],
         "im_batch_query_stats": [P, i32, P],
         "im_batch_info": [P, P],
+        "im_batch_phase_cycles": [P, P],
         "im_batch_autotune": [P, i32],
         "im_autotune_cache_save": [ctypes.c_char_p],
         "im_autotune_cache_load": [ctypes.c_char_p],
@@ -436,7 +437,8 @@ IM_OVR_UF_CAP = 2
 IM_OVR_SPREAD_LEVEL_CAP = 3
 IM_OVR_FAIL_ALLOC = 4
 IM_OVR_CELF_REFRESH_AFTER = 5
-IM_NUM_OVERRIDES = 6
+IM_OVR_BATCH_GROUP = 6
+IM_NUM_OVERRIDES = 7
 
 
 def im_debug_override(key, value):
@@ -532,6 +534,18 @@ def im_batch_info(b):
     out = np.zeros(len(BATCH_INFO), dtype=np.int64)
     _check(lib().im_batch_info(b.handle, _ptr(out)))
     return {name: int(out[i]) for i, name in enumerate(BATCH_INFO)}
+
+
+BATCH_PHASES = ("lanes", "init", "union", "compress", "gains", "celf")
+
+
+def im_batch_phase_cycles(b):
+    """{"wait": {phase: cycles}, "work": {phase: cycles}, "help": cycles} of the last run."""
+    out = np.zeros(2 * len(BATCH_PHASES) + 1, dtype=np.int64)
+    _check(lib().im_batch_phase_cycles(b.handle, _ptr(out)))
+    k = len(BATCH_PHASES)
+    return {"wait": dict(zip(BATCH_PHASES, out[:k].tolist())),
+            "work": dict(zip(BATCH_PHASES, out[k:2 * k].tolist())), "help": int(out[2 * k])}
 
 
 def im_batch_autotune(b, trials=3):
