@@ -180,19 +180,46 @@ __device__ void batch_union(const BatchInst &I, uint64_t t, uint32_t *s_boff) {
 }
 
 // Four groups of 256 threads, each its own size-memo tile (named barriers
-// 1..4); the item covers tiles [t*c, (t+1)*c).
+// 1..4), the next tile's rows loaded while the current one is walked (as in
+// the standalone size-memo kernel); the item covers tiles [t*c, (t+1)*c).
+// Root counts go straight to the root slots: a group's tiles change lanes
+// from one tile to the next, and an order that kept the lanes (so that the
+// accumulators of the standalone kernel could be used) measured slower here.
+template <int BAR>
+__device__ __forceinline__ void compress_tiles(const BatchInst &I, uint32_t k, uint32_t t1,
+                                               int32_t (*tile)[kCompL + 1], uint32_t gtid) {
+  const uint32_t tl = (I.R + kCompL - 1) / kCompL;  // tile k: vertices 32 (k / tl) .., lanes 32 (k % tl) ..
+  uint32_t tv = k / tl, tj = k % tl;
+  int32_t e[4];
+  compress_load(I.P, I.n, I.R, tv * kCompV, tj * kCompL, gtid, e);
+  for (; k < t1; k += 4) {  // a group's barrier counts its 256 threads
+    compress_stage(e, gtid, tile);
+    group_sync<BAR>();
+    uint32_t nv = tv, nj = tj + 4;
+    while (nj >= tl) {  // at most four steps
+      nj -= tl;
+      ++nv;
+    }
+    if (k + 4 < t1) compress_load(I.P, I.n, I.R, nv * kCompV, nj * kCompL, gtid, e);
+    compress_walk<BAR, false>(I.P, I.R, I.status, I.uf_cap, tv * kCompV, tj * kCompL, tile, gtid,
+                              nullptr);
+    tv = nv;
+    tj = nj;
+  }
+}
+
 __device__ void batch_compress(const BatchInst &I, uint64_t t, int32_t (*tiles)[kCompV][kCompL + 1]) {
   const uint64_t ntiles = (uint64_t)((I.n + kCompV - 1) / kCompV) * ((I.R + kCompL - 1) / kCompL);
   const uint64_t t0 = t * I.comp_chunk;
   const uint64_t t1 = t0 + I.comp_chunk < ntiles ? t0 + I.comp_chunk : ntiles;
   const uint32_t grp = threadIdx.x >> 8, gtid = threadIdx.x & 255u;
-  for (uint64_t k = t0 + grp; k < t1; k += 4) {  // a group's barrier counts its 256 threads
-    switch (grp) {
-      case 0: compress_tile<1>(I.P, I.n, I.R, I.status, I.uf_cap, k, tiles[0], gtid); break;
-      case 1: compress_tile<2>(I.P, I.n, I.R, I.status, I.uf_cap, k, tiles[1], gtid); break;
-      case 2: compress_tile<3>(I.P, I.n, I.R, I.status, I.uf_cap, k, tiles[2], gtid); break;
-      default: compress_tile<4>(I.P, I.n, I.R, I.status, I.uf_cap, k, tiles[3], gtid); break;
-    }
+  if (t0 + grp >= t1) return;
+  const uint32_t k0 = (uint32_t)(t0 + grp), k1 = (uint32_t)t1;  // n R < 2^32: tiles fit 32 bits
+  switch (grp) {
+    case 0: compress_tiles<1>(I, k0, k1, tiles[0], gtid); break;
+    case 1: compress_tiles<2>(I, k0, k1, tiles[1], gtid); break;
+    case 2: compress_tiles<3>(I, k0, k1, tiles[2], gtid); break;
+    default: compress_tiles<4>(I, k0, k1, tiles[3], gtid); break;
   }
 }
 

@@ -151,21 +151,58 @@ cudaError_t launch_union(const im_graph *g, const im_workspace *ws, const QueryP
 }
 
 // ------------------------------------------------------------------ compress
-__global__ void __launch_bounds__(256) k_compress(int32_t *P, uint32_t n, uint32_t R,
+// Eight blocks per SM (32 registers): measured faster than six or three
+// blocks with more registers.
+__global__ void __launch_bounds__(256, 8) k_compress(int32_t *P, uint32_t n, uint32_t R,
                                                   int32_t *status, uint32_t cap) {
   __shared__ int32_t tile[kCompV][kCompL + 1];
-  const uint64_t tv = (n + kCompV - 1) / kCompV, tl = (R + kCompL - 1) / kCompL;
-  const uint64_t ntiles = tv * tl;
-  for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x)
-    compress_tile<0>(P, n, R, status, cap, t, tile, threadIdx.x);
+  // tile t covers vertices 32 (t / tl) .., lanes 32 (t % tl) ..; n R < 2^32
+  // keeps the tile count within 32 bits
+  const uint32_t tl = (R + kCompL - 1) / kCompL;
+  const uint32_t ntiles = (n + kCompV - 1) / kCompV * tl;
+  uint32_t t = blockIdx.x;
+  if (t >= ntiles) return;
+  const uint32_t gq = gridDim.x / tl, gr = gridDim.x % tl;  // the grid stride in tiles
+  uint32_t tv = t / tl, tj = t % tl;
+  // The next tile's rows are loaded while the current tile's chains are
+  // walked. A prefetched slot may predate another tile's root write or root
+  // count: a parent pointer then still leads to the same root, and a root
+  // slot is still negative, so the result is the same.
+  int32_t e[4];
+  compress_load(P, n, R, tv * kCompV, tj * kCompL, threadIdx.x, e);
+  __shared__ RootAcc s_acc[8];
+  RootAcc *acc = s_acc + (threadIdx.x >> 5);
+  root_acc_clear(acc, threadIdx.x);
+  uint32_t acc_tj = tj;  // the lanes the accumulators count for
+  for (; t < ntiles; t += gridDim.x) {
+    compress_stage(e, threadIdx.x, tile);
+    group_sync<0>();
+    uint32_t nv = tv + gq, nj = tj + gr;
+    if (nj >= tl) {
+      nj -= tl;
+      ++nv;
+    }
+    if (t + gridDim.x < ntiles) compress_load(P, n, R, nv * kCompV, nj * kCompL, threadIdx.x, e);
+    if (tj != acc_tj) {
+      root_acc_flush(P, R, acc_tj * kCompL, threadIdx.x, acc);
+      acc_tj = tj;
+    }
+    compress_walk<0, true>(P, R, status, cap, tv * kCompV, tj * kCompL, tile, threadIdx.x, acc);
+    tv = nv;
+    tj = nj;
+  }
+  root_acc_flush(P, R, acc_tj * kCompL, threadIdx.x, acc);
 }
 
 cudaError_t launch_compress(const im_graph *g, const im_workspace *ws, const QueryParams &q,
                             cudaStream_t s) {
-  const uint64_t ntiles = ((uint64_t)g->n + kCompV - 1) / kCompV * ((q.R + kCompL - 1) / kCompL);
+  const uint64_t tl = (q.R + kCompL - 1) / kCompL;
+  const uint64_t ntiles = ((uint64_t)g->n + kCompV - 1) / kCompV * tl;
   uint64_t blocks = ntiles;
   const uint64_t cap = (uint64_t)g->num_sms * 8;
-  if (blocks > cap) blocks = cap;
+  // a grid of whole lane groups keeps each block on one set of lanes, so its
+  // root-count accumulators are paid once at the end
+  if (blocks > cap) blocks = cap >= tl ? cap / tl * tl : cap;
   if (blocks == 0) blocks = 1;
   k_compress<<<(unsigned)blocks, 256, 0, s>>>(ws->d_P, (uint32_t)g->n, q.R, ws->d_status,
                                               uf_budget((uint32_t)g->n));

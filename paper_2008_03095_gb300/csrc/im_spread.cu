@@ -3,8 +3,8 @@
 //
 // Bit-parallel multi-source BFS over all R samples at once: every vertex has an
 // R-bit visited mask V and a frontier mask F (bit j = internal lane j). A level
-// is a list of work chunks (a frontier vertex u and 32 of its arcs), one warp
-// per chunk, so hubs spread over many warps. The warp holds u's frontier row
+// is a list of work chunks (a frontier vertex u and the first of 32 of its
+// arcs), one warp per chunk, so hubs spread over many warps. The warp holds u's frontier row
 // in registers; for each arc u->v the edge hash selects the lane bucket that
 // can be live (the same bucket test as the component kernel), and only the
 // lanes of that bucket that are in u's frontier are tested against Eq. 2. v
@@ -26,8 +26,10 @@ namespace imgb {
 struct SpreadArgs {
   const int32_t *xadj, *adj;
   uint32_t n, R, W;
+  int32_t narcs;        // 2m
   const uint32_t *Xs, *boff;
   int nb;
+  int boff_smem;        // the bucket offsets are staged in shared memory after the randoms
   uint32_t T32;
   int all_live;
   int precheck;         // read V before each atomicOr (table larger than L2)
@@ -38,7 +40,7 @@ struct SpreadArgs {
   uint32_t *V;
   uint32_t *F[3];
   int32_t *L[3];         // frontier vertices per level (for clearing F rows)
-  uint64_t *Q[3];        // frontier work chunks per level: (vertex << 32) | chunk
+  uint64_t *Q[3];        // frontier work chunks per level: (vertex << 32) | first arc
   uint32_t *stamp;       // n: last list index (+1) a vertex was appended to
   uint32_t *cntlev;      // n + 4: frontier vertices per level
   uint32_t *chklev;      // n + 4: frontier chunks per level
@@ -68,11 +70,13 @@ __device__ __forceinline__ uint32_t lane_range_mask(uint32_t w, uint32_t j0, uin
 __device__ __forceinline__ void push_frontier(const SpreadArgs &a, int32_t v, uint32_t lev,
                                               int32_t *Ln, uint64_t *Qn) {
   Ln[atomicAdd(a.cntlev + lev, 1u)] = v;
-  const uint32_t deg = (uint32_t)(a.xadj[v + 1] - a.xadj[v]);
+  const int32_t beg = a.xadj[v];
+  const uint32_t deg = (uint32_t)(a.xadj[v + 1] - beg);
   const uint32_t nch = (deg + 31u) >> 5;
   if (nch) {
     const uint32_t at = atomicAdd(a.chklev + lev, nch);
-    for (uint32_t c = 0; c < nch; ++c) Qn[at + c] = ((uint64_t)(uint32_t)v << 32) | c;
+    for (uint32_t c = 0; c < nch; ++c)
+      Qn[at + c] = ((uint64_t)(uint32_t)v << 32) | (uint32_t)(beg + (int32_t)(c << 5));
   }
 }
 
@@ -106,8 +110,10 @@ __device__ __forceinline__ uint32_t live_lanes(uint32_t f, uint32_t w, const uin
 // frontier-bit tests then read them there instead of through L1.
 constexpr uint32_t kSpreadSmemLanes = 8192;
 
+// Two blocks per SM (at most 64 registers): measured faster than one block
+// with more registers and than three or four blocks with spills.
 template <bool OPTS>
-__global__ void __launch_bounds__(512) k_spread(SpreadArgs a) {
+__global__ void __launch_bounds__(512, 2) k_spread(SpreadArgs a) {
   extern __shared__ uint32_t sXs[];
   cg::grid_group grid = cg::this_grid();
   const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -131,6 +137,9 @@ __global__ void __launch_bounds__(512) k_spread(SpreadArgs a) {
   if (tid == 0) *a.acc = 0ull;
   if (a.xs_smem)
     for (uint32_t j = threadIdx.x; j < a.R; j += blockDim.x) sXs[j] = a.Xs[j];
+  if (a.boff_smem)
+    for (uint32_t j = threadIdx.x; j <= (1u << a.nb); j += blockDim.x) sXs[a.R + j] = a.boff[j];
+  const uint32_t *boff = a.boff_smem ? sXs + a.R : a.boff;
   grid.sync();
 
   // sources: deduplicated seed set (list 0, stamp 1), all R lanes reached
@@ -172,14 +181,21 @@ __global__ void __launch_bounds__(512) k_spread(SpreadArgs a) {
       const uint32_t cp = __ldcg(a.cntlev + level - 1);
       const int32_t *Lp = pick3(a.L[0], a.L[1], a.L[2], (level + 2) % 3);
       uint32_t *Fp = pick3(a.F[0], a.F[1], a.F[2], (level + 2) % 3);
-      for (uint64_t i = tid; i < (uint64_t)cp * W; i += nthr)
-        Fp[(uint64_t)Lp[i / W] * W + (i % W)] = 0u;
+      // a row per group of gs threads (gs a power of two, the least >= W up to 32)
+      const uint32_t lg = W >= 32u ? 5u : (uint32_t)(32 - __clz(W - 1u));
+      const uint32_t gs = 1u << lg, rows = 32u >> lg;
+      for (uint64_t k = gwarp * rows + ((uint32_t)lane >> lg); k < cp; k += nwarps * rows) {
+        const uint64_t base = (uint64_t)Lp[k] * W;
+        for (uint32_t w = (uint32_t)lane & (gs - 1u); w < W; w += gs) Fp[base + w] = 0u;
+      }
     }
-    // one warp per chunk of 32 arcs of a frontier vertex
+    // one warp per chunk of 32 arcs of a frontier vertex; the next chunk's
+    // entry is loaded while this one runs
+    uint64_t qnext = gwarp < nq ? Qc[gwarp] : 0ull;
     for (uint64_t q = gwarp; q < nq; q += nwarps) {
-      const uint64_t qe = Qc[q];
+      const uint64_t qe = qnext;
+      if (q + nwarps < nq) qnext = Qc[q + nwarps];
       const int32_t u = (int32_t)(qe >> 32);
-      const uint32_t ch = (uint32_t)qe;
       const uint32_t *fu = Fc + (uint64_t)u * W;
       // u's frontier row: word w sits in lane w & 31, register w >> 5
       uint32_t r0 = 0, r1 = 0;
@@ -187,24 +203,26 @@ __global__ void __launch_bounds__(512) k_spread(SpreadArgs a) {
         if ((uint32_t)lane < W) r0 = __ldcg(fu + lane);
         if ((uint32_t)lane + 32 < W) r1 = __ldcg(fu + lane + 32);
       }
-      const int32_t beg = a.xadj[u], end = a.xadj[u + 1];
-      const int32_t e = beg + (int32_t)(ch << 5) + lane;
+      // the chunk's arcs and u's end load together (the entry holds the first arc)
+      const uint32_t e = (uint32_t)qe + (uint32_t)lane;  // < 2^31 + 32
+      const int32_t end = a.xadj[u + 1];
+      const int32_t ve = e < (uint32_t)a.narcs ? a.adj[e] : -1;
       int32_t v = -1;
       uint32_t j0 = 0, j1 = 0, h = 0, code = 0;
-      if (e < end) {
-        v = a.adj[e];
+      if (e < (uint32_t)end) {
+        v = ve;
         if (v != u) {
           if (a.mask) {
             j1 = a.R;
           } else if (OPTS) {
             h = edge_hash(u, v);
             if (a.weighted) code = __ldg(a.code_arc + e);
-            edge_lanes(h, a.nb, a.weighted, code, a.mix, a.boff, j0, j1);
+            edge_lanes(h, a.nb, a.weighted, code, a.mix, boff, j0, j1);
           } else {
             h = edge_hash(u, v);
             const uint32_t b = lane_bucket(h, a.nb);
-            j0 = __ldg(a.boff + b);
-            j1 = __ldg(a.boff + b + 1);
+            j0 = boff[b];
+            j1 = boff[b + 1];
           }
         }
       }
@@ -266,7 +284,11 @@ __global__ void __launch_bounds__(512) k_spread(SpreadArgs a) {
       const unsigned pm = __ballot_sync(kFull, push);
       if (pm) {
         uint32_t nch = 0;
-        if (push) nch = ((uint32_t)(a.xadj[v + 1] - a.xadj[v]) + 31u) >> 5;
+        int32_t vbeg = 0;
+        if (push) {
+          vbeg = a.xadj[v];
+          nch = ((uint32_t)(a.xadj[v + 1] - vbeg) + 31u) >> 5;
+        }
         uint32_t incl = nch;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
@@ -285,7 +307,8 @@ __global__ void __launch_bounds__(512) k_spread(SpreadArgs a) {
         if (push) {
           Ln[lbase + (uint32_t)__popc(pm & ((1u << lane) - 1u))] = v;
           const uint32_t q0 = qbase + incl - nch;
-          for (uint32_t c = 0; c < nch; ++c) Qn[q0 + c] = ((uint64_t)(uint32_t)v << 32) | c;
+          for (uint32_t c = 0; c < nch; ++c)
+            Qn[q0 + c] = ((uint64_t)(uint32_t)v << 32) | (uint32_t)(vbeg + (int32_t)(c << 5));
         }
       }
     }
@@ -311,6 +334,7 @@ cudaError_t launch_spread(const im_graph *g, const im_workspace *ws, const Query
   a.n = (uint32_t)g->n;
   a.R = q.R;
   a.W = (q.R + 31) / 32;
+  a.narcs = (int32_t)(2 * g->m);
   a.Xs = ws->d_Xs;
   a.boff = ws->d_boff;
   a.nb = d_mask ? 0 : q.nb;
@@ -344,7 +368,10 @@ cudaError_t launch_spread(const im_graph *g, const im_workspace *ws, const Query
   const int64_t lo = override_value(IM_OVR_SPREAD_LEVEL_CAP);
   if (lo > 0 && (uint64_t)lo < a.level_cap) a.level_cap = (uint32_t)lo;
   a.xs_smem = (!d_mask && q.R <= kSpreadSmemLanes) ? 1 : 0;
-  const size_t smem = a.xs_smem ? (size_t)q.R * sizeof(uint32_t) : 0;
+  // the bucket offsets follow the randoms while both fit the default 48 KB
+  const size_t nboff = d_mask ? 0 : ((size_t)1 << a.nb) + 1;
+  a.boff_smem = (a.xs_smem && (q.R + nboff) * sizeof(uint32_t) <= 48 * 1024) ? 1 : 0;
+  const size_t smem = a.xs_smem ? (q.R + (a.boff_smem ? nboff : 0)) * sizeof(uint32_t) : 0;
   const void *fn = (!d_mask && (q.weighted || q.mix)) ? (const void *)k_spread<true>
                                                        : (const void *)k_spread<false>;
   int per_sm = 0;

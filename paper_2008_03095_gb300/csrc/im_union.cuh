@@ -131,92 +131,160 @@ static __device__ __forceinline__ void group_sync() {
     asm volatile("bar.sync %0, 256;" ::"r"(BAR) : "memory");
 }
 
-// Tile t (32 vertices x 32 lanes) of the size memo, by 256 threads (tid in
-// [0, 256), warp = tid / 32); tile: 32 x 33 ints of shared memory.
-template <int BAR>
-static __device__ __forceinline__ void compress_tile(int32_t *P, uint32_t n, uint32_t R, int32_t *status,
-                                              uint32_t cap, uint64_t t,
-                                              int32_t (*tile)[kCompL + 1], uint32_t tid) {
-  const uint32_t lane = tid & 31u, warp = tid >> 5;
-  const uint64_t tl = (R + kCompL - 1) / kCompL;
-  const bool vec = (R & 3u) == 0;  // rows start 16-byte aligned
-  const uint32_t v0 = (uint32_t)(t / tl) * kCompV, j0 = (uint32_t)(t % tl) * kCompL;
-  {
-    // thread: row tid / 8, lanes 4 * (tid % 8) .. + 3 of the tile
-    const uint32_t rr = tid >> 3, c0 = (tid & 7u) * 4u;
-    const uint32_t v = v0 + rr, j = j0 + c0;
-    int32_t e[4] = {-1, -1, -1, -1};
-    if (v < n) {
-      const int32_t *row = P + (uint64_t)v * R;
-      if (vec && j + 3 < R) {
-        const int4 x4 = __ldcg(reinterpret_cast<const int4 *>(row + j));
-        e[0] = x4.x; e[1] = x4.y; e[2] = x4.z; e[3] = x4.w;
-      } else {
+// The four slots of the size-memo tile at vertices v0.., lanes j0.. (32 x 32)
+// that thread tid of a 256-thread group holds: row tid / 8, lanes
+// 4 * (tid % 8) .. + 3; slots outside the table read as -1.
+static __device__ __forceinline__ void compress_load(const int32_t *P, uint32_t n, uint32_t R,
+                                                     uint32_t v0, uint32_t j0, uint32_t tid,
+                                                     int32_t (&e)[4]) {
+  const uint32_t v = v0 + (tid >> 3);
+  const uint32_t j = j0 + (tid & 7u) * 4u;
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
-          if (j + q < R) e[q] = __ldcg(row + j + q);
-      }
+  for (int q = 0; q < 4; ++q) e[q] = -1;
+  if (v < n) {
+    const int32_t *row = P + (uint64_t)v * R;
+    if ((R & 3u) == 0 && j + 3 < R) {  // rows start 16-byte aligned
+      const int4 x4 = __ldcg(reinterpret_cast<const int4 *>(row + j));
+      e[0] = x4.x; e[1] = x4.y; e[2] = x4.z; e[3] = x4.w;
+    } else {
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (j + q < R) e[q] = __ldcg(row + j + q);
     }
-#pragma unroll
-    for (int q = 0; q < 4; ++q) tile[rr][c0 + q] = e[q];
   }
-  group_sync<BAR>();
-  // warp w: tile lanes w, w + 8, w + 16, w + 24 of the 32 vertices; the
-  // first parent loads of the four items are issued together
+}
+
+static __device__ __forceinline__ void compress_stage(const int32_t (&e)[4], uint32_t tid,
+                                                      int32_t (*tile)[kCompL + 1]) {
+  const uint32_t rr = tid >> 3, c0 = (tid & 7u) * 4u;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) tile[rr][c0 + q] = e[q];
+}
+
+// Root-count accumulators of one warp's four tile lanes, in shared memory
+// (written by the warp's lane 0 only): in a giant component every tile of a
+// lane adds to the same root slot, and those atomics pile onto one L2 slice.
+// Each warp instead keeps, per lane, the count owed to the smallest root it
+// has met, and pays it with one atomic when the root changes, when the warp
+// moves to other lanes, or at the end (the root slot only decreases, so it
+// reads negative throughout).
+struct RootAcc {
+  uint32_t root[4];  // 0xFFFFFFFF: none
+  int32_t cnt[4];
+};
+
+static __device__ __forceinline__ void root_acc_clear(RootAcc *acc, uint32_t tid) {
+  if ((tid & 31u) == 0) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      acc->root[q] = 0xffffffffu;
+      acc->cnt[q] = 0;
+    }
+  }
+  __syncwarp();
+}
+
+// Pays the counts owed at tile lanes j0 + warp + 8q and clears them.
+static __device__ __forceinline__ void root_acc_flush(int32_t *P, uint32_t R, uint32_t j0,
+                                                      uint32_t tid, RootAcc *acc) {
+  const uint32_t warp = (tid >> 5) & 7u;
+  __syncwarp();
+  if ((tid & 31u) == 0) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (acc->cnt[q]) atomicAdd(P + (uint64_t)acc->root[q] * R + (j0 + warp + 8u * q), -acc->cnt[q]);
+      acc->root[q] = 0xffffffffu;
+      acc->cnt[q] = 0;
+    }
+  }
+  __syncwarp();
+}
+
+// The tile at vertices v0.., lanes j0.., staged in shared memory, by 256
+// threads: each non-root slot is pointed at its root and counted into the
+// root slot. Warp w takes tile lanes w, w + 8, w + 16, w + 24 of the 32
+// vertices; a thread's four parent chains advance together, one load of each
+// per step, so a tile costs as many dependent loads as its longest chain.
+// With ACC, counts go to the warp's accumulator (acc, for these lanes) or to
+// one atomic per other distinct root of the warp; without, every distinct
+// root of the warp takes one atomic. Ends with the group's barrier (the tile
+// may be restaged after it).
+template <int BAR, bool ACC>
+static __device__ __forceinline__ void compress_walk(int32_t *P, uint32_t R, int32_t *status,
+                                                     uint32_t cap, uint32_t v0, uint32_t j0,
+                                                     int32_t (*tile)[kCompL + 1], uint32_t tid,
+                                                     RootAcc *acc) {
+  const uint32_t lane = tid & 31u, warp = tid >> 5;
   const uint32_t v = v0 + lane;
   int32_t x[4], r[4];
-  bool live[4];
+  bool live[4], act[4];
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     x[q] = tile[lane][warp + 8u * q];
     r[q] = x[q];
-    live[q] = x[q] >= 0;  // out-of-range slots were loaded as -1
+    live[q] = x[q] >= 0;  // roots, and slots outside the table, are negative
+    act[q] = live[q];
   }
-  int32_t y[4];
+  // r[q] holds a non-root vertex of the chain while act[q]; its slot is read
+  // next, and a negative slot marks r[q] as the root
+  for (uint32_t it = 0;; ++it) {
+    int32_t z[4];
 #pragma unroll
-  for (int q = 0; q < 4; ++q)
-    y[q] = live[q] ? __ldcg(P + (uint64_t)(uint32_t)r[q] * R + (j0 + warp + 8u * q)) : -1;
+    for (int q = 0; q < 4; ++q)
+      z[q] = act[q] ? __ldcg(P + (uint64_t)(uint32_t)r[q] * R + (j0 + warp + 8u * q)) : -1;
+    bool more = false;
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const uint32_t j = j0 + warp + 8u * q;
-    if (live[q] && y[q] >= 0) {  // parent is not the root: follow the chain
-      r[q] = y[q];
-      uint32_t it = 1;
-      for (; it < cap; ++it) {
-        const int32_t z = __ldcg(P + (uint64_t)(uint32_t)r[q] * R + j);
-        if (z < 0) break;
-        r[q] = z;
+    for (int q = 0; q < 4; ++q) {
+      if (act[q] && z[q] >= 0) {
+        r[q] = z[q];
+        more = true;
+      } else {
+        act[q] = false;
       }
-      if (it == cap) {
-        set_status(status, IM_ETIMEOUT);
-        live[q] = false;
-      } else if (it > 1) {
-        // Full path compression: the chain's inner nodes (non-roots of the
-        // same component) get the root too, so later walks through them
-        // take one step. Their own slots are written with the same value
-        // when their tiles come round, so no update is lost.
-        int32_t z = x[q];  // the first parent; the walk stops at the root
-        for (uint32_t k = 0; k < it && z != r[q]; ++k) {
-          const int32_t nz = __ldcg(P + (uint64_t)(uint32_t)z * R + j);
-          if (nz < 0) break;
-          __stcg(P + (uint64_t)(uint32_t)z * R + j, r[q]);
-          z = nz;
-        }
-      }
+    }
+    if (!more) break;
+    if (it + 1 >= cap) {  // longer than any chain of n vertices: a corrupt table
+      set_status(status, IM_ETIMEOUT);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) live[q] = live[q] && !act[q];
+      break;
     }
   }
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     const uint32_t j = j0 + warp + 8u * q;
-    const uint32_t key = live[q] ? (uint32_t)r[q] : 0xffffffffu;
+    if (!ACC) {
+      const uint32_t key = live[q] ? (uint32_t)r[q] : 0xffffffffu;
+      const unsigned peers = __match_any_sync(kFull, key);
+      if (live[q]) {
+        if (lane == (uint32_t)(__ffs(peers) - 1))
+          atomicAdd(P + (uint64_t)(uint32_t)r[q] * R + j, -(int32_t)__popc(peers));
+        if (r[q] != x[q]) __stcg(P + (uint64_t)v * R + j, r[q]);
+      }
+      continue;
+    }
+    uint32_t ar = acc->root[q];  // read by every lane before lane 0 may write
+    const uint32_t m = __reduce_min_sync(kFull, live[q] ? (uint32_t)r[q] : 0xffffffffu);
+    if (m < ar) {  // a smaller root: pay the old one, follow the new one
+      if (lane == 0) {
+        if (acc->cnt[q]) atomicAdd(P + (uint64_t)ar * R + j, -acc->cnt[q]);
+        acc->root[q] = m;
+        acc->cnt[q] = 0;
+      }
+      ar = m;
+    }
+    const bool mine = live[q] && (uint32_t)r[q] == ar;
+    const unsigned mm = __ballot_sync(kFull, mine);
+    if (lane == 0 && mm) acc->cnt[q] += __popc(mm);
+    const uint32_t key = (live[q] && !mine) ? (uint32_t)r[q] : 0xffffffffu;
     const unsigned peers = __match_any_sync(kFull, key);
     if (live[q]) {
-      if (lane == (uint32_t)(__ffs(peers) - 1))
+      if (!mine && lane == (uint32_t)(__ffs(peers) - 1))
         atomicAdd(P + (uint64_t)(uint32_t)r[q] * R + j, -(int32_t)__popc(peers));
       if (r[q] != x[q]) __stcg(P + (uint64_t)v * R + j, r[q]);
     }
   }
-  group_sync<BAR>();  // the tile is reloaded next iteration
+  group_sync<BAR>();  // the tile is restaged next
 }
 
 }  // namespace imgb
