@@ -265,6 +265,9 @@ def algorithmic_bytes(phase, n, m_up, R, T):
     if phase == "union":
         live = m_up * R * (T / 2.0 ** 32)
         return 8 * m_up + 8 * live  # edge list + both endpoint slots per live arc-lane
+    if phase == "spread_cc":  # the spread's hand-over: table init, union, count
+        return (algorithmic_bytes("prep", n, m_up, R, T) + algorithmic_bytes("union", n, m_up, R, T)
+                + 4 * nR + nR / 8)  # the count reads every slot and the marked-root bits
     return None
 
 
@@ -473,9 +476,12 @@ def measure(name, w, xadj, adj, steps, warmup, world, detail):
                          "cluster launch",
                     traffic=None)
     else:
-        if dominant == "union":
-            b = statistics.mean(algorithmic_bytes("union", n, g_m_up(xadj, adj), R, T[p])
+        handed_over = all(by_p[str(p)]["per_query"].get("spread_components", 0) >= 1 for p in ps)
+        if dominant in ("union", "spread_cc"):
+            b = statistics.mean(algorithmic_bytes(dominant, n, g_m_up(xadj, adj), R, T[p])
                                 for p in ps)
+            if dominant == "spread_cc" and not handed_over:
+                b = None
         else:
             b = algorithmic_bytes(dominant, n, 0, R, 0)
         if b is None:  # spread: per-level work varies; report its time only

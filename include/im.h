@@ -367,7 +367,12 @@ enum {
   IM_STAT_CHECK_CODE = 13,       /* first failed internal invariant check (0 = none) */
   IM_STAT_CHECK_V0 = 14,         /* ... and two values describing it */
   IM_STAT_CHECK_V1 = 15,
-  IM_NUM_STATS = 16
+  IM_STAT_SPREAD_COMPONENTS = 16, /* spread estimates finished from the samples' components
+                                     (a BFS frontier passed n/16 vertices, on a table larger
+                                     than L2 with n R < 112 m) */
+  IM_STAT_MEMO_ACCUMULATORS = 17, /* size memos run with per-warp root-count accumulators (a
+                                     sampled component held more than 4.5% of the vertices) */
+  IM_NUM_STATS = 18
 };
 /* out: host array of IM_NUM_STATS int64 values. */
 int im_workspace_stats(im_workspace *ws, int64_t *out);
@@ -399,7 +404,10 @@ enum {
   IM_PHASE_CELF = 4,         /* on-device lazy greedy */
   IM_PHASE_SPREAD_PREP = 5,  /* X_r draw and lane order for the spread */
   IM_PHASE_SPREAD = 6,       /* bit-parallel multi-source BFS */
-  IM_NUM_PHASES = 7
+  IM_PHASE_SPREAD_CC = 7,    /* the spread's hand-over to components: union, seed roots, count
+                                (queued behind the BFS where a hand-over can pay; returns at
+                                once unless the BFS handed over, having initialised the table) */
+  IM_NUM_PHASES = 8
 };
 
 /* on != 0 starts recording (and clears earlier records); 0 stops. */

@@ -321,7 +321,8 @@ def im_workspace_status(ws):
 STATS = ("celf_rounds", "celf_evaluations", "celf_extractions", "spread_levels",
          "celf_cycles_extract", "celf_cycles_eval", "celf_cycles_commit", "celf_cycles_merge",
          "celf_refreshes", "celf_cycles_commits", "celf_cycles_cover", "celf_refreshed",
-         "celf_cycles_refresh", "check_code", "check_v0", "check_v1")
+         "celf_cycles_refresh", "check_code", "check_v0", "check_v1", "spread_components",
+         "memo_accumulators")
 
 
 def im_workspace_stats(ws):
@@ -344,7 +345,7 @@ def im_sampling_threshold(p):
     return int(out.value)
 
 
-PHASES = ("prep", "union", "compress", "gains", "celf", "spread_prep", "spread")
+PHASES = ("prep", "union", "compress", "gains", "celf", "spread_prep", "spread", "spread_cc")
 
 
 def im_profile_enable(on=True):

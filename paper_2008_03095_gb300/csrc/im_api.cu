@@ -269,13 +269,14 @@ int ws_create(const im_graph *g, int32_t R_max, im_workspace **out) {
   WS_ALLOC(d_Q2, n + (size_t)g->m / 16 + 1);
   WS_ALLOC(d_inlist, n);
   WS_ALLOC(d_cnt, 2 * (n + 4));
-  WS_ALLOC(d_acc, 1);
+  WS_ALLOC(d_acc, 6);  // spread: sigma, hand-over word, block counter; size-memo probe: 3
   WS_ALLOC(d_stats, IM_NUM_STATS);
   WS_ALLOC(d_status, 1);
   WS_ALLOC(d_seeds_out, n);
   WS_ALLOC(d_sigma_out, n);
 #undef WS_ALLOC
   if (e == cudaSuccess) e = cudaMemset(ws->d_status, 0, sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMemset(ws->d_acc, 0, 6 * sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMemset(ws->d_stats, 0, sizeof(unsigned long long) * IM_NUM_STATS);
   if (e != cudaSuccess) {
     ws_free(ws);
@@ -318,15 +319,37 @@ int enqueue_select(const im_graph *g, const im_workspace *ws, int32_t K, const Q
   return IM_OK;
 }
 
+// The spread (Algorithm 4 on the fixed samples): the BFS, and on tables larger
+// than L2 the hand-over kernels behind it (they return at once unless the BFS
+// handed over; see im_spread.cu).
 int enqueue_spread(const im_graph *g, const im_workspace *ws, const int32_t *d_seeds, int32_t ns,
                    const QueryParams &q, const uint8_t *d_mask, uint64_t *d_sigma, cudaStream_t s) {
   QueryParams qq = q;
   if (d_mask) qq.nb = 0;
+  // The hand-over pays when the table exceeds L2 and the BFS's cost per
+  // vertex (its arcs, rescanned on about five levels at 65 ps per arc scan)
+  // beats the components' (R slots at about 5.7 ps each): 112 m > n R.
+  const uint64_t nR = (uint64_t)g->n * qq.R;
+  const bool handover = ws->d_P && ws->d_cov && !qq.none_live && g->m_up > 0 &&
+                        nR * sizeof(int32_t) > (uint64_t)g->l2_bytes &&
+                        nR < 112ull * (uint64_t)g->m;
   API_CUDA(timed(IM_PHASE_SPREAD_PREP, s, [&] { return launch_prep(ws, qq, false, false, s); }),
            "k_prep");
   API_CUDA(timed(IM_PHASE_SPREAD, s,
-                 [&] { return launch_spread(g, ws, qq, d_seeds, ns, d_mask, d_sigma, s); }),
+                 [&] { return launch_spread(g, ws, qq, d_seeds, ns, d_mask, d_sigma, handover, s); }),
            "k_spread");
+  if (handover) {
+    const unsigned long long *gate = ws->d_acc + 1;
+    API_CUDA(timed(IM_PHASE_SPREAD_CC, s,
+                   [&] {
+                     cudaError_t e = launch_union(g, ws, qq, d_mask, s, gate);
+                     if (e == cudaSuccess) e = launch_spread_cc(g, ws, qq, d_seeds, ns, d_sigma, s);
+                     if (e == cudaSuccess)  // three kernels: union, mark, count
+                       for (int k = 0; k < 2; ++k) api_count_launch();
+                     return e;
+                   }),
+             "spread hand-over");
+  }
   return IM_OK;
 }
 
@@ -498,7 +521,7 @@ int fused_sampling_select(im_graph *g, im_workspace *ws, int32_t K, const QueryP
       v1.d_Xs = ws->d_X + r;
       e = timed(IM_PHASE_SPREAD, s, [&] {
         return launch_spread(g, &v1, q1, ws->d_seeds_in, (int)Su.size(), nullptr,
-                             reinterpret_cast<uint64_t *>(d_acc) + r, s);
+                             reinterpret_cast<uint64_t *>(d_acc) + r, false, s);
       });
     }
     if (e == cudaSuccess)

@@ -169,6 +169,7 @@ __device__ void batch_union(const BatchInst &I, uint64_t t, uint32_t *s_boff) {
   u.mask = nullptr;
   u.xadj = nullptr;
   u.adj = nullptr;
+  u.gate = nullptr;
   const int nbk = 1 << I.nb;
   for (int i = threadIdx.x; i <= nbk; i += blockDim.x) s_boff[i] = __ldcg(I.boff + i);
   __syncthreads();
@@ -201,8 +202,7 @@ __device__ __forceinline__ void compress_tiles(const BatchInst &I, uint32_t k, u
       ++nv;
     }
     if (k + 4 < t1) compress_load(I.P, I.n, I.R, nv * kCompV, nj * kCompL, gtid, e);
-    compress_walk<BAR, false>(I.P, I.R, I.status, I.uf_cap, tv * kCompV, tj * kCompL, tile, gtid,
-                              nullptr);
+    compress_walk<BAR>(I.P, I.R, I.status, I.uf_cap, tv * kCompV, tj * kCompL, tile, gtid);
     tv = nv;
     tj = nj;
   }

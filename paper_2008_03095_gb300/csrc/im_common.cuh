@@ -288,8 +288,10 @@ int api_enqueue_spread(const im_graph *g, const im_workspace *ws, const int32_t 
 // All launchers queue work on `s` and return the launch error (if any).
 cudaError_t launch_prep(const im_workspace *ws, const QueryParams &q, bool init_table,
                         bool zero_cov, cudaStream_t s);
+// gate: a device word; the kernel returns at once while it is 0 (null: runs).
 cudaError_t launch_union(const im_graph *g, const im_workspace *ws, const QueryParams &q,
-                         const uint8_t *d_mask, cudaStream_t s);
+                         const uint8_t *d_mask, cudaStream_t s,
+                         const unsigned long long *gate = nullptr);
 cudaError_t launch_compress(const im_graph *g, const im_workspace *ws, const QueryParams &q,
                             cudaStream_t s);
 cudaError_t launch_gains(const im_graph *g, const im_workspace *ws, const QueryParams &q,
@@ -303,9 +305,15 @@ cudaError_t launch_edge_hash(const int32_t *d_u, const int32_t *d_v, int64_t cou
                              uint32_t *d_h, cudaStream_t s);
 cudaError_t launch_celf(const im_graph *g, const im_workspace *ws, const QueryParams &q, int K,
                         int32_t *d_seeds, uint64_t *d_sigma, cudaStream_t s);
+// handover: the BFS may hand over (through ws->d_acc[1]): it then initialises
+// the label table and the covered bitmap, and launch_union (gated) and
+// launch_spread_cc must be queued behind it.
 cudaError_t launch_spread(const im_graph *g, const im_workspace *ws, const QueryParams &q,
                           const int32_t *d_seeds, int num_seeds, const uint8_t *d_mask,
-                          uint64_t *d_sigma, cudaStream_t s);
+                          uint64_t *d_sigma, bool handover, cudaStream_t s);
+cudaError_t launch_spread_cc(const im_graph *g, const im_workspace *ws, const QueryParams &q,
+                             const int32_t *d_seeds, int num_seeds, uint64_t *d_sigma,
+                             cudaStream_t s);
 // FusedSampling variant: single-lane table reset and mg accumulation
 cudaError_t launch_fs_init(const im_graph *g, int32_t *P1, cudaStream_t s);
 cudaError_t launch_fs_accum(const im_graph *g, const int32_t *P1, unsigned long long *mg,

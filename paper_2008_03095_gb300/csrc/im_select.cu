@@ -101,6 +101,7 @@ cudaError_t launch_prep(const im_workspace *ws, const QueryParams &q, bool init_
 template <bool MASKED, bool OPTS>
 __global__ void __launch_bounds__(256) k_union(UnionArgs a) {
   extern __shared__ uint32_t s_boff[];
+  if (a.gate && __ldcg(a.gate) == 0ull) return;
   if (!MASKED) {
     const int nbk = 1 << a.nb;
     for (int i = threadIdx.x; i <= nbk; i += blockDim.x) s_boff[i] = a.boff[i];
@@ -113,7 +114,7 @@ __global__ void __launch_bounds__(256) k_union(UnionArgs a) {
 }
 
 cudaError_t launch_union(const im_graph *g, const im_workspace *ws, const QueryParams &q,
-                         const uint8_t *d_mask, cudaStream_t s) {
+                         const uint8_t *d_mask, cudaStream_t s, const unsigned long long *gate) {
   if (g->m_up == 0) return cudaSuccess;
   UnionArgs a;
   a.eu = g->d_eu;
@@ -134,6 +135,7 @@ cudaError_t launch_union(const im_graph *g, const im_workspace *ws, const QueryP
   a.weighted = q.weighted;
   a.mix = q.mix;
   a.code_up = g->d_code_up;
+  a.gate = gate;
   int64_t warps_needed = (g->m_up + 31) / 32;
   int64_t blocks = (warps_needed + 7) / 8;
   int64_t cap = (int64_t)g->num_sms * 8;
@@ -151,17 +153,87 @@ cudaError_t launch_union(const im_graph *g, const im_workspace *ws, const QueryP
 }
 
 // ------------------------------------------------------------------ compress
+// The size memo's walk depends on the samples: where a sample holds a large
+// component (a share of the vertices above kMemoAccShare), nearly every tile
+// of a lane adds to its root slot, those atomics pile onto one L2 slice, and
+// the warps' root-count accumulators pay (on the 4M-vertex power-law graph,
+// 7.6 vs 9.7 ms); where components are small, the plain walk with path
+// compression does the least work per slot (the clustered 335k-vertex graph:
+// 1.36 vs 2.07 ms). A one-block-per-lane probe estimates the share from the
+// union-find table before the size memo: in kProbeLanes lanes spread over R,
+// kProbeVertices vertices (a multiplicative hash of the index) are walked to
+// their roots and the most frequent root's count is summed; the last block
+// writes the choice. 16 x 256 samples put the estimate within about 0.3% of
+// the share near the threshold.
+constexpr uint32_t kProbeLanes = 16, kProbeVertices = 256;
+constexpr double kMemoAccShare = 0.045;
+
+__global__ void __launch_bounds__(kProbeVertices) k_memo_probe(const int32_t *P, uint32_t n,
+                                                               uint32_t R, uint32_t cap,
+                                                               int32_t *status,
+                                                               unsigned long long *probe,
+                                                               unsigned long long *stats) {
+  // probe[0]: the choice (1 = accumulators); [1]: summed mode counts; [2]: blocks done
+  __shared__ uint32_t s_root[kProbeVertices];
+  __shared__ uint32_t s_max[kProbeVertices / 32];
+  __shared__ bool s_last;
+  const uint32_t j = (uint32_t)(((uint64_t)blockIdx.x * R) / gridDim.x);
+  const uint32_t v = (uint32_t)(((uint64_t)threadIdx.x * 2654435761u + blockIdx.x) % n);
+  uint32_t r = v;
+  int32_t x = __ldcg(P + (uint64_t)v * R + j);
+  for (uint32_t it = 0; x >= 0; ++it) {
+    if (it >= cap) {
+      set_status(status, IM_ETIMEOUT);
+      break;
+    }
+    r = (uint32_t)x;
+    x = __ldcg(P + (uint64_t)r * R + j);
+  }
+  s_root[threadIdx.x] = r;
+  __syncthreads();
+  uint32_t c = 0;
+  for (uint32_t k = 0; k < kProbeVertices; ++k) c += s_root[k] == r;
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) {
+    const uint32_t o = __shfl_xor_sync(kFull, c, d);
+    c = o > c ? o : c;
+  }
+  if ((threadIdx.x & 31) == 0) s_max[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t m = 0;
+    for (uint32_t w = 0; w < kProbeVertices / 32; ++w) m = s_max[w] > m ? s_max[w] : m;
+    atomicAdd(probe + 1, (unsigned long long)m);
+    __threadfence();
+    s_last = atomicAdd(probe + 2, 1ull) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (s_last && threadIdx.x == 0) {
+    __threadfence();
+    const double share = (double)__ldcg(probe + 1) / ((double)gridDim.x * kProbeVertices);
+    probe[0] = share > kMemoAccShare ? 1ull : 0ull;
+    if (probe[0] && stats) atomicAdd(stats + IM_STAT_MEMO_ACCUMULATORS, 1ull);
+    probe[1] = 0ull;
+    probe[2] = 0ull;
+  }
+}
+
 // Eight blocks per SM (32 registers): measured faster than six or three
-// blocks with more registers.
+// blocks with more registers. Both instances are queued; the one *mode (from
+// k_memo_probe) does not pick returns at once (holding both walks in one
+// kernel, behind a run-time branch or as two non-inlined loops, compiled the
+// accumulator walk 3-45% slower). Tile t covers vertices 32 (t / tl) ..,
+// lanes 32 (t % tl) ..; n R < 2^32 keeps the tile count within 32 bits.
+template <bool ACC>
 __global__ void __launch_bounds__(256, 8) k_compress(int32_t *P, uint32_t n, uint32_t R,
-                                                  int32_t *status, uint32_t cap) {
+                                                     int32_t *status, uint32_t cap,
+                                                     const unsigned long long *mode) {
   __shared__ int32_t tile[kCompV][kCompL + 1];
-  // tile t covers vertices 32 (t / tl) .., lanes 32 (t % tl) ..; n R < 2^32
-  // keeps the tile count within 32 bits
+  __shared__ RootAcc s_acc[ACC ? 8 : 1];
   const uint32_t tl = (R + kCompL - 1) / kCompL;
   const uint32_t ntiles = (n + kCompV - 1) / kCompV * tl;
   uint32_t t = blockIdx.x;
-  if (t >= ntiles) return;
+  if (t >= ntiles || (__ldcg(mode) != 0ull) != ACC) return;
   const uint32_t gq = gridDim.x / tl, gr = gridDim.x % tl;  // the grid stride in tiles
   uint32_t tv = t / tl, tj = t % tl;
   // The next tile's rows are loaded while the current tile's chains are
@@ -170,9 +242,8 @@ __global__ void __launch_bounds__(256, 8) k_compress(int32_t *P, uint32_t n, uin
   // slot is still negative, so the result is the same.
   int32_t e[4];
   compress_load(P, n, R, tv * kCompV, tj * kCompL, threadIdx.x, e);
-  __shared__ RootAcc s_acc[8];
-  RootAcc *acc = s_acc + (threadIdx.x >> 5);
-  root_acc_clear(acc, threadIdx.x);
+  RootAcc *acc = s_acc + (ACC ? (threadIdx.x >> 5) : 0);
+  if (ACC) root_acc_clear(acc, threadIdx.x);
   uint32_t acc_tj = tj;  // the lanes the accumulators count for
   for (; t < ntiles; t += gridDim.x) {
     compress_stage(e, threadIdx.x, tile);
@@ -183,29 +254,45 @@ __global__ void __launch_bounds__(256, 8) k_compress(int32_t *P, uint32_t n, uin
       ++nv;
     }
     if (t + gridDim.x < ntiles) compress_load(P, n, R, nv * kCompV, nj * kCompL, threadIdx.x, e);
-    if (tj != acc_tj) {
-      root_acc_flush(P, R, acc_tj * kCompL, threadIdx.x, acc);
-      acc_tj = tj;
+    if (ACC) {
+      if (tj != acc_tj) {
+        root_acc_flush(P, R, acc_tj * kCompL, threadIdx.x, acc);
+        acc_tj = tj;
+      }
+      compress_walk_acc<0>(P, R, status, cap, tv * kCompV, tj * kCompL, tile, threadIdx.x, acc);
+    } else {
+      compress_walk<0>(P, R, status, cap, tv * kCompV, tj * kCompL, tile, threadIdx.x);
     }
-    compress_walk<0, true>(P, R, status, cap, tv * kCompV, tj * kCompL, tile, threadIdx.x, acc);
     tv = nv;
     tj = nj;
   }
-  root_acc_flush(P, R, acc_tj * kCompL, threadIdx.x, acc);
+  if (ACC) root_acc_flush(P, R, acc_tj * kCompL, threadIdx.x, acc);
 }
 
 cudaError_t launch_compress(const im_graph *g, const im_workspace *ws, const QueryParams &q,
                             cudaStream_t s) {
+  unsigned long long *probe = ws->d_acc + 3;
+  const uint32_t cap = uf_budget((uint32_t)g->n);
+  k_memo_probe<<<kProbeLanes, kProbeVertices, 0, s>>>(ws->d_P, (uint32_t)g->n, q.R, cap,
+                                                      ws->d_status, probe, ws->d_stats);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  api_count_launch();
   const uint64_t tl = (q.R + kCompL - 1) / kCompL;
   const uint64_t ntiles = ((uint64_t)g->n + kCompV - 1) / kCompV * tl;
   uint64_t blocks = ntiles;
-  const uint64_t cap = (uint64_t)g->num_sms * 8;
+  const uint64_t bcap = (uint64_t)g->num_sms * 8;
   // a grid of whole lane groups keeps each block on one set of lanes, so its
   // root-count accumulators are paid once at the end
-  if (blocks > cap) blocks = cap >= tl ? cap / tl * tl : cap;
+  if (blocks > bcap) blocks = bcap >= tl ? bcap / tl * tl : bcap;
   if (blocks == 0) blocks = 1;
-  k_compress<<<(unsigned)blocks, 256, 0, s>>>(ws->d_P, (uint32_t)g->n, q.R, ws->d_status,
-                                              uf_budget((uint32_t)g->n));
+  k_compress<true><<<(unsigned)blocks, 256, 0, s>>>(ws->d_P, (uint32_t)g->n, q.R, ws->d_status,
+                                                    cap, probe);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  api_count_launch();
+  k_compress<false><<<(unsigned)blocks, 256, 0, s>>>(ws->d_P, (uint32_t)g->n, q.R, ws->d_status,
+                                                     cap, probe);
   return cudaGetLastError();
 }
 

@@ -15,9 +15,24 @@
 // suffices: level L reads F[L%3], writes F[(L+1)%3] and clears the rows of
 // the level L-1 frontier in F[(L+2)%3]. Per-level counters and level stamps
 // (instead of reset flags) build the frontier lists.
+//
+// The spread is reachability, not distance: BFS levels are only a schedule.
+// A vertex reached at different depths in different samples is on several
+// levels' frontiers and its arcs are scanned once per such level, so a seed
+// set whose samples reach a giant component costs several scans of most of
+// the graph. On tables larger than L2 the BFS therefore hands over when a
+// frontier exceeds n/16 vertices (where the BFS's arcs per vertex, times the
+// levels that rescan them, outweigh the R slots per vertex the components
+// cost; the caller decides): the BFS initialises the label table, the
+// components of every sample are formed by union-find (each edge once, the
+// select path's kernel), the seeds' roots are marked in each sample, and
+// every slot whose root is marked is counted. The hand-over kernels are
+// queued behind every such BFS and return at once unless it handed over, so
+// the choice costs no host round trip.
 #include <cooperative_groups.h>
 
 #include "im_common.cuh"
+#include "im_union.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -49,6 +64,10 @@ struct SpreadArgs {
   int32_t *status;
   unsigned long long *stats;
   uint32_t level_cap;    // budget of BFS levels (a BFS has at most n levels)
+  unsigned long long *gate;  // hand-over word (null: the BFS always finishes)
+  uint32_t handover;     // a frontier of more vertices hands over
+  int32_t *P;            // hand-over: the label table (n R, set to -1) and the
+  uint32_t *cov;         // marked-root bitmap (n R bits, cleared)
   int weighted, mix;     // sampling options: per-arc codes, mixed hash
   const uint32_t *code_arc;
 };
@@ -134,7 +153,10 @@ __global__ void __launch_bounds__(512, 2) k_spread(SpreadArgs a) {
     a.cntlev[i] = 0u;
     a.chklev[i] = 0u;
   }
-  if (tid == 0) *a.acc = 0ull;
+  if (tid == 0) {
+    *a.acc = 0ull;
+    if (a.gate) *a.gate = 0ull;
+  }
   if (a.xs_smem)
     for (uint32_t j = threadIdx.x; j < a.R; j += blockDim.x) sXs[j] = a.Xs[j];
   if (a.boff_smem)
@@ -169,6 +191,21 @@ __global__ void __launch_bounds__(512, 2) k_spread(SpreadArgs a) {
   for (; level < a.level_cap; ++level) {
     const uint32_t cc = __ldcg(a.cntlev + level);
     if (cc == 0) break;
+    if (a.gate && cc > a.handover) {  // the same decision in every thread
+      if (tid == 0) {
+        *a.gate = 1ull;
+        if (a.stats) atomicAdd(a.stats + 3, (unsigned long long)level);
+      }
+      const uint64_t nR = (uint64_t)a.n * a.R;
+      const int4 m1 = make_int4(-1, -1, -1, -1);
+      for (uint64_t i = tid; i < (nR >> 2); i += nthr) reinterpret_cast<int4 *>(a.P)[i] = m1;
+      for (uint64_t i = ((nR >> 2) << 2) + tid; i < nR; i += nthr) a.P[i] = -1;
+      const uint64_t nc = (nR + 31) >> 5;
+      const uint4 z = make_uint4(0, 0, 0, 0);
+      for (uint64_t i = tid; i < (nc >> 2); i += nthr) reinterpret_cast<uint4 *>(a.cov)[i] = z;
+      for (uint64_t i = ((nc >> 2) << 2) + tid; i < nc; i += nthr) a.cov[i] = 0u;
+      return;
+    }
     const uint32_t nq = __ldcg(a.chklev + level);
     const uint64_t *Qc = pick3(a.Q[0], a.Q[1], a.Q[2], level % 3);
     int32_t *Ln = pick3(a.L[0], a.L[1], a.L[2], (level + 1) % 3);
@@ -325,9 +362,136 @@ __global__ void __launch_bounds__(512, 2) k_spread(SpreadArgs a) {
   }
 }
 
+// ------------------------------------------------------------ hand-over path
+struct SpreadCcArgs {
+  int32_t *P;
+  uint32_t n, R, cap;
+  uint32_t *cov;         // marked roots: bit (root R + lane)
+  const int32_t *seeds;
+  int num_seeds;
+  unsigned long long *acc, *gate, *done;
+  uint64_t *out;
+  int32_t *status;
+  unsigned long long *stats;
+};
+
+// The root of every seed in every sample is marked (a seed set counts each
+// component once however many seeds it holds).
+__global__ void __launch_bounds__(256) k_spread_mark(SpreadCcArgs a) {
+  if (__ldcg(a.gate) == 0ull) return;
+  const uint64_t total = (uint64_t)a.num_seeds * a.R;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    const int32_t s = a.seeds[i / a.R];
+    const uint32_t j = (uint32_t)(i % a.R);
+    if (s < 0 || (uint32_t)s >= a.n) continue;  // the BFS recorded IM_EINVAL
+    uint32_t r = (uint32_t)s;
+    int32_t x = __ldcg(a.P + (uint64_t)r * a.R + j);
+    for (uint32_t it = 0; x >= 0; ++it) {
+      if (it >= a.cap) {
+        set_status(a.status, IM_ETIMEOUT);
+        break;
+      }
+      r = (uint32_t)x;
+      x = __ldcg(a.P + (uint64_t)r * a.R + j);
+    }
+    const uint64_t bit = (uint64_t)r * a.R + j;
+    atomicOr(a.cov + (bit >> 5), 1u << (bit & 31u));
+  }
+}
+
+// sigmaR = the slots whose root is marked, in tiles of 32 vertices x 32 lanes
+// (the size memo's tiles, read only); the last block writes the result.
+__global__ void __launch_bounds__(256, 8) k_spread_count(SpreadCcArgs a) {
+  __shared__ int32_t tile[kCompV][kCompL + 1];
+  __shared__ unsigned long long s_sum[8];
+  __shared__ bool s_last;
+  if (__ldcg(a.gate) == 0ull) return;
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  const uint32_t tl = (a.R + kCompL - 1) / kCompL;
+  const uint32_t ntiles = (a.n + kCompV - 1) / kCompV * tl;  // n R < 2^32
+  uint64_t cnt = 0;
+  int32_t e[4];  // the next tile's slots, loaded while the current one is walked
+  if (blockIdx.x < ntiles)
+    compress_load(a.P, a.n, a.R, blockIdx.x / tl * kCompV, blockIdx.x % tl * kCompL, threadIdx.x, e);
+  for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const uint32_t v0 = t / tl * kCompV, j0 = t % tl * kCompL;
+    compress_stage(e, threadIdx.x, tile);
+    __syncthreads();
+    const uint32_t tn = t + gridDim.x;
+    if (tn < ntiles) compress_load(a.P, a.n, a.R, tn / tl * kCompV, tn % tl * kCompL, threadIdx.x, e);
+    int32_t x[4], r[4];
+    bool live[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) x[q] = tile[lane][warp + 8u * q];
+    walk_roots(a.P, a.R, a.status, a.cap, j0 + warp, x, r, live);
+    const uint32_t v = v0 + lane;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const uint32_t j = j0 + warp + 8u * q;
+      // a negative slot inside the table is a root: the vertex itself
+      const bool root_self = x[q] < 0 && v < a.n && j < a.R;
+      if (live[q] || root_self) {
+        const uint64_t bit = (uint64_t)(live[q] ? (uint32_t)r[q] : v) * a.R + j;
+        cnt += (__ldcg(a.cov + (bit >> 5)) >> (bit & 31u)) & 1u;
+      }
+    }
+    __syncthreads();  // the tile is restaged next
+  }
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) cnt += __shfl_xor_sync(kFull, cnt, d);
+  if (lane == 0) s_sum[warp] = cnt;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long b = 0;
+    for (int w = 0; w < 8; ++w) b += s_sum[w];
+    if (b) atomicAdd(a.acc, b);
+    __threadfence();
+    s_last = atomicAdd(a.done, 1ull) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (s_last && threadIdx.x == 0) {
+    __threadfence();
+    *a.out = (uint64_t)__ldcg(a.acc);
+    *a.done = 0ull;
+    if (a.stats) atomicAdd(a.stats + IM_STAT_SPREAD_COMPONENTS, 1ull);
+  }
+}
+
+cudaError_t launch_spread_cc(const im_graph *g, const im_workspace *ws, const QueryParams &q,
+                             const int32_t *d_seeds, int num_seeds, uint64_t *d_sigma,
+                             cudaStream_t s) {
+  SpreadCcArgs a;
+  a.P = ws->d_P;
+  a.n = (uint32_t)g->n;
+  a.R = q.R;
+  a.cap = uf_budget((uint32_t)g->n);
+  a.cov = ws->d_cov;
+  a.seeds = d_seeds;
+  a.num_seeds = num_seeds;
+  a.acc = ws->d_acc;
+  a.gate = ws->d_acc + 1;
+  a.done = ws->d_acc + 2;
+  a.out = d_sigma;
+  a.status = ws->d_status;
+  a.stats = ws->d_stats;
+  const uint64_t pairs = (uint64_t)num_seeds * q.R;
+  uint64_t mb = (pairs + 255) / 256;
+  if (mb > (uint64_t)g->num_sms * 4) mb = (uint64_t)g->num_sms * 4;
+  if (mb == 0) mb = 1;
+  k_spread_mark<<<(unsigned)mb, 256, 0, s>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const uint64_t ntiles = ((uint64_t)g->n + kCompV - 1) / kCompV * ((q.R + kCompL - 1) / kCompL);
+  uint64_t blocks = ntiles;
+  if (blocks > (uint64_t)g->num_sms * 8) blocks = (uint64_t)g->num_sms * 8;
+  k_spread_count<<<(unsigned)blocks, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_spread(const im_graph *g, const im_workspace *ws, const QueryParams &q,
                           const int32_t *d_seeds, int num_seeds, const uint8_t *d_mask,
-                          uint64_t *d_sigma, cudaStream_t s) {
+                          uint64_t *d_sigma, bool handover, cudaStream_t s) {
   SpreadArgs a;
   a.xadj = g->d_xadj;
   a.adj = g->d_adj;
@@ -365,6 +529,10 @@ cudaError_t launch_spread(const im_graph *g, const im_workspace *ws, const Query
   a.mix = q.mix;
   a.code_arc = g->d_code_arc;
   a.level_cap = (uint32_t)g->n + 2u;
+  a.gate = handover ? ws->d_acc + 1 : nullptr;
+  a.handover = (uint32_t)(g->n / 16);
+  a.P = ws->d_P;
+  a.cov = ws->d_cov;
   const int64_t lo = override_value(IM_OVR_SPREAD_LEVEL_CAP);
   if (lo > 0 && (uint64_t)lo < a.level_cap) a.level_cap = (uint32_t)lo;
   a.xs_smem = (!d_mask && q.R <= kSpreadSmemLanes) ? 1 : 0;

@@ -25,6 +25,7 @@ struct UnionArgs {
   // explicit-mask mode (test hook)
   const uint8_t *mask;
   const int32_t *xadj, *adj;
+  const unsigned long long *gate;  // k_union returns at once while *gate == 0 (null: runs)
 };
 
 template <bool COH>
@@ -161,6 +162,49 @@ static __device__ __forceinline__ void compress_stage(const int32_t (&e)[4], uin
   for (int q = 0; q < 4; ++q) tile[rr][c0 + q] = e[q];
 }
 
+// The roots of four slots x[q] of one thread, at lanes jw + 8q (a parent, or
+// negative for a root or a slot outside the table): r[q] = the root and
+// live[q] set for every non-negative x[q]. The four chains advance together,
+// one load of each per step, so they cost as many dependent loads as the
+// longest. A chain longer than cap (longer than any chain of n vertices: a
+// corrupt table) records IM_ETIMEOUT and leaves its slot not live.
+static __device__ __forceinline__ void walk_roots(const int32_t *P, uint32_t R, int32_t *status,
+                                                  uint32_t cap, uint32_t jw, const int32_t (&x)[4],
+                                                  int32_t (&r)[4], bool (&live)[4]) {
+  bool act[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    r[q] = x[q];
+    live[q] = x[q] >= 0;
+    act[q] = live[q];
+  }
+  // r[q] holds a non-root vertex of the chain while act[q]; its slot is read
+  // next, and a negative slot marks r[q] as the root
+  for (uint32_t it = 0;; ++it) {
+    int32_t z[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      z[q] = act[q] ? __ldcg(P + (uint64_t)(uint32_t)r[q] * R + (jw + 8u * q)) : -1;
+    bool more = false;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (act[q] && z[q] >= 0) {
+        r[q] = z[q];
+        more = true;
+      } else {
+        act[q] = false;
+      }
+    }
+    if (!more) break;
+    if (it + 1 >= cap) {
+      set_status(status, IM_ETIMEOUT);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) live[q] = live[q] && !act[q];
+      break;
+    }
+  }
+}
+
 // Root-count accumulators of one warp's four tile lanes, in shared memory
 // (written by the warp's lane 0 only): in a giant component every tile of a
 // lane adds to the same root slot, and those atomics pile onto one L2 slice.
@@ -201,68 +245,28 @@ static __device__ __forceinline__ void root_acc_flush(int32_t *P, uint32_t R, ui
 }
 
 // The tile at vertices v0.., lanes j0.., staged in shared memory, by 256
-// threads: each non-root slot is pointed at its root and counted into the
-// root slot. Warp w takes tile lanes w, w + 8, w + 16, w + 24 of the 32
-// vertices; a thread's four parent chains advance together, one load of each
-// per step, so a tile costs as many dependent loads as its longest chain.
-// With ACC, counts go to the warp's accumulator (acc, for these lanes) or to
-// one atomic per other distinct root of the warp; without, every distinct
-// root of the warp takes one atomic. Ends with the group's barrier (the tile
-// may be restaged after it).
-template <int BAR, bool ACC>
-static __device__ __forceinline__ void compress_walk(int32_t *P, uint32_t R, int32_t *status,
-                                                     uint32_t cap, uint32_t v0, uint32_t j0,
-                                                     int32_t (*tile)[kCompL + 1], uint32_t tid,
-                                                     RootAcc *acc) {
+// threads, with the warp's root-count accumulators (acc, for these lanes):
+// each non-root slot is pointed at its root and counted, into the
+// accumulator when the root is the warp's accumulated one, else with one
+// atomic per distinct root of the warp. Warp w takes tile lanes w, w + 8,
+// w + 16, w + 24 of the 32 vertices (walk_roots). Where a sample holds a
+// large component, its root recurs in nearly every tile of a lane. Ends with
+// the group's barrier (the tile may be restaged after it).
+template <int BAR>
+static __device__ __forceinline__ void compress_walk_acc(int32_t *P, uint32_t R, int32_t *status,
+                                                         uint32_t cap, uint32_t v0, uint32_t j0,
+                                                         int32_t (*tile)[kCompL + 1], uint32_t tid,
+                                                         RootAcc *acc) {
   const uint32_t lane = tid & 31u, warp = tid >> 5;
   const uint32_t v = v0 + lane;
   int32_t x[4], r[4];
-  bool live[4], act[4];
+  bool live[4];
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    x[q] = tile[lane][warp + 8u * q];
-    r[q] = x[q];
-    live[q] = x[q] >= 0;  // roots, and slots outside the table, are negative
-    act[q] = live[q];
-  }
-  // r[q] holds a non-root vertex of the chain while act[q]; its slot is read
-  // next, and a negative slot marks r[q] as the root
-  for (uint32_t it = 0;; ++it) {
-    int32_t z[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-      z[q] = act[q] ? __ldcg(P + (uint64_t)(uint32_t)r[q] * R + (j0 + warp + 8u * q)) : -1;
-    bool more = false;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      if (act[q] && z[q] >= 0) {
-        r[q] = z[q];
-        more = true;
-      } else {
-        act[q] = false;
-      }
-    }
-    if (!more) break;
-    if (it + 1 >= cap) {  // longer than any chain of n vertices: a corrupt table
-      set_status(status, IM_ETIMEOUT);
-#pragma unroll
-      for (int q = 0; q < 4; ++q) live[q] = live[q] && !act[q];
-      break;
-    }
-  }
+  for (int q = 0; q < 4; ++q) x[q] = tile[lane][warp + 8u * q];
+  walk_roots(P, R, status, cap, j0 + warp, x, r, live);
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     const uint32_t j = j0 + warp + 8u * q;
-    if (!ACC) {
-      const uint32_t key = live[q] ? (uint32_t)r[q] : 0xffffffffu;
-      const unsigned peers = __match_any_sync(kFull, key);
-      if (live[q]) {
-        if (lane == (uint32_t)(__ffs(peers) - 1))
-          atomicAdd(P + (uint64_t)(uint32_t)r[q] * R + j, -(int32_t)__popc(peers));
-        if (r[q] != x[q]) __stcg(P + (uint64_t)v * R + j, r[q]);
-      }
-      continue;
-    }
     uint32_t ar = acc->root[q];  // read by every lane before lane 0 may write
     const uint32_t m = __reduce_min_sync(kFull, live[q] ? (uint32_t)r[q] : 0xffffffffu);
     if (m < ar) {  // a smaller root: pay the old one, follow the new one
@@ -280,6 +284,72 @@ static __device__ __forceinline__ void compress_walk(int32_t *P, uint32_t R, int
     const unsigned peers = __match_any_sync(kFull, key);
     if (live[q]) {
       if (!mine && lane == (uint32_t)(__ffs(peers) - 1))
+        atomicAdd(P + (uint64_t)(uint32_t)r[q] * R + j, -(int32_t)__popc(peers));
+      if (r[q] != x[q]) __stcg(P + (uint64_t)v * R + j, r[q]);
+    }
+  }
+  group_sync<BAR>();  // the tile is restaged next
+}
+
+// The tile at vertices v0.., lanes j0.., by 256 threads, without
+// accumulators: a thread's four chains are walked one after another, and a
+// chain of two or more links is compressed (its inner vertices get the root
+// too, so later walks through them take one step; their own slots are
+// written with the same value when their tiles come round, so no update is
+// lost). Each distinct root of a warp takes one atomic. Where samples hold
+// no large component, chains are short and rarely shared: the walk with the
+// least work per slot is the fastest.
+template <int BAR>
+static __device__ __forceinline__ void compress_walk(int32_t *P, uint32_t R, int32_t *status,
+                                                     uint32_t cap, uint32_t v0, uint32_t j0,
+                                                     int32_t (*tile)[kCompL + 1], uint32_t tid) {
+  const uint32_t lane = tid & 31u, warp = tid >> 5;
+  const uint32_t v = v0 + lane;
+  int32_t x[4], r[4];
+  bool live[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    x[q] = tile[lane][warp + 8u * q];
+    r[q] = x[q];
+    live[q] = x[q] >= 0;  // roots, and slots outside the table, are negative
+  }
+  // the first parent loads of the four items are issued together
+  int32_t y[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    y[q] = live[q] ? __ldcg(P + (uint64_t)(uint32_t)r[q] * R + (j0 + warp + 8u * q)) : -1;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const uint32_t j = j0 + warp + 8u * q;
+    if (live[q] && y[q] >= 0) {  // the parent is not the root: follow the chain
+      r[q] = y[q];
+      uint32_t it = 1;
+      for (; it < cap; ++it) {
+        const int32_t z = __ldcg(P + (uint64_t)(uint32_t)r[q] * R + j);
+        if (z < 0) break;
+        r[q] = z;
+      }
+      if (it == cap) {
+        set_status(status, IM_ETIMEOUT);
+        live[q] = false;
+      } else if (it > 1) {
+        int32_t z = x[q];  // the first parent; the walk stops at the root
+        for (uint32_t k = 0; k < it && z != r[q]; ++k) {
+          const int32_t nz = __ldcg(P + (uint64_t)(uint32_t)z * R + j);
+          if (nz < 0) break;
+          __stcg(P + (uint64_t)(uint32_t)z * R + j, r[q]);
+          z = nz;
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const uint32_t j = j0 + warp + 8u * q;
+    const uint32_t key = live[q] ? (uint32_t)r[q] : 0xffffffffu;
+    const unsigned peers = __match_any_sync(kFull, key);
+    if (live[q]) {
+      if (lane == (uint32_t)(__ffs(peers) - 1))
         atomicAdd(P + (uint64_t)(uint32_t)r[q] * R + j, -(int32_t)__popc(peers));
       if (r[q] != x[q]) __stcg(P + (uint64_t)v * R + j, r[q]);
     }

@@ -7,7 +7,9 @@ a fixed seed set (k_prep, k_spread through im_estimate_spread), each
     python -m paper_2008_03095_gb300.profile_case --workload powerlaw_n37154 --p 0.05
 
 The seed set of the spread is the K highest-degree vertices (lowest id first
-on equal degree). Prints one JSON line with the per-phase event times.
+on equal degree), or with `--selected-seeds` the seeds that im_select_seeds
+picks (selected once, before the profiled runs). Prints one JSON line with
+the per-phase event times.
 """
 import argparse
 import json
@@ -28,6 +30,8 @@ def main(argv=None):
     ap.add_argument("--chung-lu", default=None,
                     help="n,m,gamma,seed: a Chung-Lu graph instead of a named workload")
     ap.add_argument("--R", type=int, default=None)
+    ap.add_argument("--selected-seeds", action="store_true",
+                    help="spread the seeds im_select_seeds picks instead of the top-degree ones")
     args = ap.parse_args(argv)
 
     sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
@@ -52,6 +56,9 @@ def main(argv=None):
     seeds = np.argsort(-deg, kind="stable")[:K].astype(np.int32)
     torch.cuda.set_device(0)
     g = im.im_graph_create(xadj, adj)
+    if args.selected_seeds:
+        seeds, _ = im.im_select_seeds(g, K, R, p, seed)
+        seeds = np.ascontiguousarray(seeds, dtype=np.int32)
     mg = np.zeros(1, dtype=np.uint64)
     if args.spread_only:
         ws = im.im_workspace_create(g, R)
