@@ -265,9 +265,6 @@ def algorithmic_bytes(phase, n, m_up, R, T):
     if phase == "union":
         live = m_up * R * (T / 2.0 ** 32)
         return 8 * m_up + 8 * live  # edge list + both endpoint slots per live arc-lane
-    if phase == "spread_cc":  # the spread's hand-over: table init, union, count
-        return (algorithmic_bytes("prep", n, m_up, R, T) + algorithmic_bytes("union", n, m_up, R, T)
-                + 4 * nR + nR / 8)  # the count reads every slot and the marked-root bits
     return None
 
 
@@ -454,13 +451,24 @@ def measure(name, w, xadj, adj, steps, warmup, world, detail):
         return rec, (seeds_h, sigma_h, spread_h)
 
     rec["clocks"] = clock_info
-    # Roofline of the dominant kernel (largest share of device time).
-    dominant = max(prof, key=lambda k: prof[k][0])
+    # Roofline of the dominant kernel (largest share of device time). The
+    # spread's hand-over runs the select path's union and size memo again
+    # (phases spread_union, spread_compress): they count toward those kernels
+    # when every query handed over, so that every launch did the full work.
+    handed_over = all(by_p[str(p)]["per_query"].get("spread_components", 0) >= 1 for p in ps)
+    kern = {}
+    for ph, (ms, cnt) in prof.items():
+        k = {"spread_union": "union", "spread_compress": "compress"}.get(ph, ph)
+        if k != ph and not handed_over:
+            continue
+        a, c = kern.get(k, (0.0, 0))
+        kern[k] = (a + ms, c + cnt)
+    dominant = max(kern, key=lambda k: kern[k][0])
     T = {p: im.im_sampling_threshold(p) for p in ps}
-    avg_s = prof[dominant][0] / prof[dominant][1] / 1e3
+    avg_s = kern[dominant][0] / kern[dominant][1] / 1e3
     roof = {"kernel": "k_" + dominant, "bound": "hbm", "peak": peak, "unit": "GB/s",
-            "peak_kind": peak_kind, "avg_launch_us": avg_s * 1e6,
-            "share_of_device_time": prof[dominant][0] / tot if tot else None}
+            "peak_kind": peak_kind, "avg_launch_us": avg_s * 1e6, "launches": kern[dominant][1],
+            "share_of_device_time": kern[dominant][0] / tot if tot else None}
     if dominant == "celf":
         q = [by_p[str(p)]["per_query"] for p in ps]
         mb = statistics.mean(celf_method_bytes(n, R, x["celf_evaluations"], x["celf_extractions"])
@@ -476,12 +484,9 @@ def measure(name, w, xadj, adj, steps, warmup, world, detail):
                          "cluster launch",
                     traffic=None)
     else:
-        handed_over = all(by_p[str(p)]["per_query"].get("spread_components", 0) >= 1 for p in ps)
-        if dominant in ("union", "spread_cc"):
-            b = statistics.mean(algorithmic_bytes(dominant, n, g_m_up(xadj, adj), R, T[p])
+        if dominant == "union":
+            b = statistics.mean(algorithmic_bytes("union", n, g_m_up(xadj, adj), R, T[p])
                                 for p in ps)
-            if dominant == "spread_cc" and not handed_over:
-                b = None
         else:
             b = algorithmic_bytes(dominant, n, 0, R, 0)
         if b is None:  # spread: per-level work varies; report its time only

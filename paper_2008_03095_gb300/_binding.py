@@ -345,7 +345,8 @@ def im_sampling_threshold(p):
     return int(out.value)
 
 
-PHASES = ("prep", "union", "compress", "gains", "celf", "spread_prep", "spread", "spread_cc")
+PHASES = ("prep", "union", "compress", "gains", "celf", "spread_prep", "spread", "spread_cc",
+          "spread_union", "spread_compress")
 
 
 def im_profile_enable(on=True):

@@ -338,17 +338,17 @@ int enqueue_spread(const im_graph *g, const im_workspace *ws, const int32_t *d_s
   API_CUDA(timed(IM_PHASE_SPREAD, s,
                  [&] { return launch_spread(g, ws, qq, d_seeds, ns, d_mask, d_sigma, handover, s); }),
            "k_spread");
-  if (handover) {
+  if (handover) {  // each returns at once unless the BFS handed over
     const unsigned long long *gate = ws->d_acc + 1;
+    API_CUDA(timed(IM_PHASE_SPREAD_UNION, s,
+                   [&] { return launch_union(g, ws, qq, d_mask, s, gate); }),
+             "k_union (spread)");
+    API_CUDA(timed(IM_PHASE_SPREAD_COMPRESS, s,
+                   [&] { return launch_compress(g, ws, qq, s, gate); }),
+             "k_compress (spread)");
     API_CUDA(timed(IM_PHASE_SPREAD_CC, s,
-                   [&] {
-                     cudaError_t e = launch_union(g, ws, qq, d_mask, s, gate);
-                     if (e == cudaSuccess) e = launch_spread_cc(g, ws, qq, d_seeds, ns, d_sigma, s);
-                     if (e == cudaSuccess)  // three kernels: union, mark, count
-                       for (int k = 0; k < 2; ++k) api_count_launch();
-                     return e;
-                   }),
-             "spread hand-over");
+                   [&] { return launch_spread_cc(g, ws, qq, d_seeds, ns, d_sigma, s); }),
+             "k_spread_sum");
   }
   return IM_OK;
 }

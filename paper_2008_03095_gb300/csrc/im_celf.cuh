@@ -277,7 +277,7 @@ __device__ __forceinline__ uint32_t exact_gain(const CelfArgs &a, uint32_t v) {
   const uint32_t R = a.R;
   const int32_t *row = a.P + (size_t)v * R;
   uint32_t g = 0;
-#pragma unroll 4
+#pragma unroll 8
   for (uint32_t j = lane; j < R; j += 32) {
     const int32_t x = ld_label<COH>(row + j);
     const uint32_t root = x < 0 ? v : (uint32_t)x;

@@ -293,7 +293,7 @@ cudaError_t launch_union(const im_graph *g, const im_workspace *ws, const QueryP
                          const uint8_t *d_mask, cudaStream_t s,
                          const unsigned long long *gate = nullptr);
 cudaError_t launch_compress(const im_graph *g, const im_workspace *ws, const QueryParams &q,
-                            cudaStream_t s);
+                            cudaStream_t s, const unsigned long long *gate = nullptr);
 cudaError_t launch_gains(const im_graph *g, const im_workspace *ws, const QueryParams &q,
                          cudaStream_t s);
 cudaError_t launch_expand(const im_graph *g, const im_workspace *ws, const QueryParams &q,
@@ -306,8 +306,8 @@ cudaError_t launch_edge_hash(const int32_t *d_u, const int32_t *d_v, int64_t cou
 cudaError_t launch_celf(const im_graph *g, const im_workspace *ws, const QueryParams &q, int K,
                         int32_t *d_seeds, uint64_t *d_sigma, cudaStream_t s);
 // handover: the BFS may hand over (through ws->d_acc[1]): it then initialises
-// the label table and the covered bitmap, and launch_union (gated) and
-// launch_spread_cc must be queued behind it.
+// the label table and the covered bitmap, and launch_union, launch_compress
+// (both gated by ws->d_acc + 1) and launch_spread_cc must be queued behind it.
 cudaError_t launch_spread(const im_graph *g, const im_workspace *ws, const QueryParams &q,
                           const int32_t *d_seeds, int num_seeds, const uint8_t *d_mask,
                           uint64_t *d_sigma, bool handover, cudaStream_t s);

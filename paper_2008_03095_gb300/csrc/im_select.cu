@@ -172,11 +172,17 @@ __global__ void __launch_bounds__(kProbeVertices) k_memo_probe(const int32_t *P,
                                                                uint32_t R, uint32_t cap,
                                                                int32_t *status,
                                                                unsigned long long *probe,
-                                                               unsigned long long *stats) {
-  // probe[0]: the choice (1 = accumulators); [1]: summed mode counts; [2]: blocks done
+                                                               unsigned long long *stats,
+                                                               const unsigned long long *gate) {
+  // probe[0]: the choice (1 = accumulators, 0 = path compression, 2 = no size
+  // memo: the gate is closed); [1]: summed mode counts; [2]: blocks done
   __shared__ uint32_t s_root[kProbeVertices];
   __shared__ uint32_t s_max[kProbeVertices / 32];
   __shared__ bool s_last;
+  if (gate && __ldcg(gate) == 0ull) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) probe[0] = 2ull;
+    return;
+  }
   const uint32_t j = (uint32_t)(((uint64_t)blockIdx.x * R) / gridDim.x);
   const uint32_t v = (uint32_t)(((uint64_t)threadIdx.x * 2654435761u + blockIdx.x) % n);
   uint32_t r = v;
@@ -220,7 +226,7 @@ __global__ void __launch_bounds__(kProbeVertices) k_memo_probe(const int32_t *P,
 
 // Eight blocks per SM (32 registers): measured faster than six or three
 // blocks with more registers. Both instances are queued; the one *mode (from
-// k_memo_probe) does not pick returns at once (holding both walks in one
+// k_memo_probe: 1 accumulators, 0 path compression) does not pick returns at once (holding both walks in one
 // kernel, behind a run-time branch or as two non-inlined loops, compiled the
 // accumulator walk 3-45% slower). Tile t covers vertices 32 (t / tl) ..,
 // lanes 32 (t % tl) ..; n R < 2^32 keeps the tile count within 32 bits.
@@ -233,7 +239,7 @@ __global__ void __launch_bounds__(256, 8) k_compress(int32_t *P, uint32_t n, uin
   const uint32_t tl = (R + kCompL - 1) / kCompL;
   const uint32_t ntiles = (n + kCompV - 1) / kCompV * tl;
   uint32_t t = blockIdx.x;
-  if (t >= ntiles || (__ldcg(mode) != 0ull) != ACC) return;
+  if (t >= ntiles || __ldcg(mode) != (ACC ? 1ull : 0ull)) return;
   const uint32_t gq = gridDim.x / tl, gr = gridDim.x % tl;  // the grid stride in tiles
   uint32_t tv = t / tl, tj = t % tl;
   // The next tile's rows are loaded while the current tile's chains are
@@ -270,11 +276,11 @@ __global__ void __launch_bounds__(256, 8) k_compress(int32_t *P, uint32_t n, uin
 }
 
 cudaError_t launch_compress(const im_graph *g, const im_workspace *ws, const QueryParams &q,
-                            cudaStream_t s) {
+                            cudaStream_t s, const unsigned long long *gate) {
   unsigned long long *probe = ws->d_acc + 3;
   const uint32_t cap = uf_budget((uint32_t)g->n);
   k_memo_probe<<<kProbeLanes, kProbeVertices, 0, s>>>(ws->d_P, (uint32_t)g->n, q.R, cap,
-                                                      ws->d_status, probe, ws->d_stats);
+                                                      ws->d_status, probe, ws->d_stats, gate);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   api_count_launch();

@@ -24,15 +24,14 @@
 // frontier exceeds n/16 vertices (where the BFS's arcs per vertex, times the
 // levels that rescan them, outweigh the R slots per vertex the components
 // cost; the caller decides): the BFS initialises the label table, the
-// components of every sample are formed by union-find (each edge once, the
-// select path's kernel), the seeds' roots are marked in each sample, and
-// every slot whose root is marked is counted. The hand-over kernels are
-// queued behind every such BFS and return at once unless it handed over, so
-// the choice costs no host round trip.
+// components of every sample and their sizes are formed by the select path's
+// union-find and size memo (each edge once, each slot once), and sigmaR sums,
+// in every sample, the sizes of the distinct components holding a seed. The
+// hand-over kernels are queued behind every such BFS and return at once
+// unless it handed over, so the choice costs no host round trip.
 #include <cooperative_groups.h>
 
 #include "im_common.cuh"
-#include "im_union.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -363,84 +362,42 @@ __global__ void __launch_bounds__(512, 2) k_spread(SpreadArgs a) {
 }
 
 // ------------------------------------------------------------ hand-over path
-struct SpreadCcArgs {
-  int32_t *P;
-  uint32_t n, R, cap;
-  uint32_t *cov;         // marked roots: bit (root R + lane)
+struct SpreadSumArgs {
+  const int32_t *P;      // size memo: a root slot holds -|C|, any other slot its root
+  uint32_t n, R;
+  uint32_t *cov;         // marked roots: bit (root R + lane), cleared by the BFS
   const int32_t *seeds;
   int num_seeds;
   unsigned long long *acc, *gate, *done;
   uint64_t *out;
-  int32_t *status;
   unsigned long long *stats;
 };
 
-// The root of every seed in every sample is marked (a seed set counts each
-// component once however many seeds it holds).
-__global__ void __launch_bounds__(256) k_spread_mark(SpreadCcArgs a) {
+// sigmaR = sum over samples of the sizes of the distinct components holding a
+// seed: every (seed, lane) pair finds its root (one step in the size memo)
+// and marks it; the pair that sets the mark adds the component's size. The
+// last block writes the result.
+__global__ void __launch_bounds__(256) k_spread_sum(SpreadSumArgs a) {
+  __shared__ unsigned long long s_sum[8];
+  __shared__ bool s_last;
   if (__ldcg(a.gate) == 0ull) return;
   const uint64_t total = (uint64_t)a.num_seeds * a.R;
+  unsigned long long sum = 0;
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
        i += (uint64_t)gridDim.x * blockDim.x) {
     const int32_t s = a.seeds[i / a.R];
     const uint32_t j = (uint32_t)(i % a.R);
     if (s < 0 || (uint32_t)s >= a.n) continue;  // the BFS recorded IM_EINVAL
-    uint32_t r = (uint32_t)s;
-    int32_t x = __ldcg(a.P + (uint64_t)r * a.R + j);
-    for (uint32_t it = 0; x >= 0; ++it) {
-      if (it >= a.cap) {
-        set_status(a.status, IM_ETIMEOUT);
-        break;
-      }
-      r = (uint32_t)x;
-      x = __ldcg(a.P + (uint64_t)r * a.R + j);
-    }
+    const int32_t x = __ldcg(a.P + (uint64_t)(uint32_t)s * a.R + j);
+    const uint32_t r = x < 0 ? (uint32_t)s : (uint32_t)x;
+    const int32_t sz = x < 0 ? x : __ldcg(a.P + (uint64_t)r * a.R + j);
     const uint64_t bit = (uint64_t)r * a.R + j;
-    atomicOr(a.cov + (bit >> 5), 1u << (bit & 31u));
-  }
-}
-
-// sigmaR = the slots whose root is marked, in tiles of 32 vertices x 32 lanes
-// (the size memo's tiles, read only); the last block writes the result.
-__global__ void __launch_bounds__(256, 8) k_spread_count(SpreadCcArgs a) {
-  __shared__ int32_t tile[kCompV][kCompL + 1];
-  __shared__ unsigned long long s_sum[8];
-  __shared__ bool s_last;
-  if (__ldcg(a.gate) == 0ull) return;
-  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
-  const uint32_t tl = (a.R + kCompL - 1) / kCompL;
-  const uint32_t ntiles = (a.n + kCompV - 1) / kCompV * tl;  // n R < 2^32
-  uint64_t cnt = 0;
-  int32_t e[4];  // the next tile's slots, loaded while the current one is walked
-  if (blockIdx.x < ntiles)
-    compress_load(a.P, a.n, a.R, blockIdx.x / tl * kCompV, blockIdx.x % tl * kCompL, threadIdx.x, e);
-  for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const uint32_t v0 = t / tl * kCompV, j0 = t % tl * kCompL;
-    compress_stage(e, threadIdx.x, tile);
-    __syncthreads();
-    const uint32_t tn = t + gridDim.x;
-    if (tn < ntiles) compress_load(a.P, a.n, a.R, tn / tl * kCompV, tn % tl * kCompL, threadIdx.x, e);
-    int32_t x[4], r[4];
-    bool live[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) x[q] = tile[lane][warp + 8u * q];
-    walk_roots(a.P, a.R, a.status, a.cap, j0 + warp, x, r, live);
-    const uint32_t v = v0 + lane;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const uint32_t j = j0 + warp + 8u * q;
-      // a negative slot inside the table is a root: the vertex itself
-      const bool root_self = x[q] < 0 && v < a.n && j < a.R;
-      if (live[q] || root_self) {
-        const uint64_t bit = (uint64_t)(live[q] ? (uint32_t)r[q] : v) * a.R + j;
-        cnt += (__ldcg(a.cov + (bit >> 5)) >> (bit & 31u)) & 1u;
-      }
-    }
-    __syncthreads();  // the tile is restaged next
+    const uint32_t m = 1u << (bit & 31u);
+    if (!(atomicOr(a.cov + (bit >> 5), m) & m)) sum += (unsigned long long)(uint32_t)(-sz);
   }
 #pragma unroll
-  for (int d = 16; d > 0; d >>= 1) cnt += __shfl_xor_sync(kFull, cnt, d);
-  if (lane == 0) s_sum[warp] = cnt;
+  for (int d = 16; d > 0; d >>= 1) sum += __shfl_xor_sync(kFull, sum, d);
+  if ((threadIdx.x & 31) == 0) s_sum[threadIdx.x >> 5] = sum;
   __syncthreads();
   if (threadIdx.x == 0) {
     unsigned long long b = 0;
@@ -461,11 +418,10 @@ __global__ void __launch_bounds__(256, 8) k_spread_count(SpreadCcArgs a) {
 cudaError_t launch_spread_cc(const im_graph *g, const im_workspace *ws, const QueryParams &q,
                              const int32_t *d_seeds, int num_seeds, uint64_t *d_sigma,
                              cudaStream_t s) {
-  SpreadCcArgs a;
+  SpreadSumArgs a;
   a.P = ws->d_P;
   a.n = (uint32_t)g->n;
   a.R = q.R;
-  a.cap = uf_budget((uint32_t)g->n);
   a.cov = ws->d_cov;
   a.seeds = d_seeds;
   a.num_seeds = num_seeds;
@@ -473,19 +429,12 @@ cudaError_t launch_spread_cc(const im_graph *g, const im_workspace *ws, const Qu
   a.gate = ws->d_acc + 1;
   a.done = ws->d_acc + 2;
   a.out = d_sigma;
-  a.status = ws->d_status;
   a.stats = ws->d_stats;
   const uint64_t pairs = (uint64_t)num_seeds * q.R;
-  uint64_t mb = (pairs + 255) / 256;
-  if (mb > (uint64_t)g->num_sms * 4) mb = (uint64_t)g->num_sms * 4;
-  if (mb == 0) mb = 1;
-  k_spread_mark<<<(unsigned)mb, 256, 0, s>>>(a);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  const uint64_t ntiles = ((uint64_t)g->n + kCompV - 1) / kCompV * ((q.R + kCompL - 1) / kCompL);
-  uint64_t blocks = ntiles;
-  if (blocks > (uint64_t)g->num_sms * 8) blocks = (uint64_t)g->num_sms * 8;
-  k_spread_count<<<(unsigned)blocks, 256, 0, s>>>(a);
+  uint64_t blocks = (pairs + 255) / 256;
+  if (blocks > (uint64_t)g->num_sms * 4) blocks = (uint64_t)g->num_sms * 4;
+  if (blocks == 0) blocks = 1;
+  k_spread_sum<<<(unsigned)blocks, 256, 0, s>>>(a);
   return cudaGetLastError();
 }
 
