@@ -491,7 +491,9 @@ enum {
   IM_OVR_CELF_REFRESH_AFTER = 5, /* lazy greedy: exact evaluations without a commit before all
                                     gains are recomputed (any value keeps the result exact) */
   IM_OVR_BATCH_GROUP = 6,        /* batches planned from now: queries per schedule group */
-  IM_NUM_OVERRIDES = 7
+  IM_OVR_CELF_EXT_REFRESH = 7,   /* lazy greedy's bulk refresh as a launch of its own: 1 always,
+                                    2 never (0: above 2^20 vertices) */
+  IM_NUM_OVERRIDES = 8
 };
 /* Errors: IM_EINVAL (unknown key, or a value outside the key's range). */
 int im_debug_override(int32_t key, int64_t value);

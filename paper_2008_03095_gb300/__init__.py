@@ -11,6 +11,7 @@ from ._binding import (IM_EBUSY, IM_ECUDA, IM_EINTERNAL, IM_EINVAL, IM_ENOMEM, I
                        im_debug_tables_lanes, im_debug_override, im_debug_clear_overrides, im_debug_first_gains,
                        IM_OVR_CELF_CLUSTER, IM_OVR_CELF_ROUND_CAP, IM_OVR_UF_CAP,
                        IM_OVR_SPREAD_LEVEL_CAP, IM_OVR_FAIL_ALLOC, IM_OVR_CELF_REFRESH_AFTER, IM_OVR_BATCH_GROUP,
+                       IM_OVR_CELF_EXT_REFRESH,
                        IM_NUM_OVERRIDES, IM_SAMPLE_EDGE_WEIGHTS, IM_SAMPLE_MIXED_HASH,
                        IM_ALGO_FUSED_SAMPLING, im_graph_create_weighted, im_select_seeds_ex,
                        im_estimate_spread_ex, im_select_seeds_ex_async,

@@ -440,7 +440,8 @@ IM_OVR_SPREAD_LEVEL_CAP = 3
 IM_OVR_FAIL_ALLOC = 4
 IM_OVR_CELF_REFRESH_AFTER = 5
 IM_OVR_BATCH_GROUP = 6
-IM_NUM_OVERRIDES = 7
+IM_OVR_CELF_EXT_REFRESH = 7
+IM_NUM_OVERRIDES = 8
 
 
 def im_debug_override(key, value):

@@ -42,6 +42,10 @@
 namespace imgb {
 
 size_t celf_ctl_bytes() { return sizeof(CelfCtl); }
+
+// Above this many vertices the lazy greedy's bulk refresh runs as a launch of
+// its own (k_celf_refresh).
+constexpr uint32_t kExtRefreshMinN = 1u << 20;
 int celf_pool_size(uint32_t R) {
   const size_t per = (size_t)R * 8;
   size_t b = kPoolSmemBudget / per;
@@ -69,18 +73,9 @@ __global__ void __launch_bounds__(kCelfThreads, 1) k_celf(CelfArgs a) {
   uint32_t *pcont = proot + (size_t)a.B * R;
   CelfCtl *ctl = a.ctl;
   const bool local_extract = a.n <= kLocalN;
-
-  for (uint32_t i = gtid; i < 3 * kBins; i += gthreads) (&ctl->hist[0][0])[i] = 0u;
-  for (uint32_t i = gtid; i < a.n; i += gthreads) a.chosen[i] = 0;
-  if (gtid == 0) {
-    ctl->kmin = ~0ull;
-    ctl->kmax = 0ull;
-    ctl->kcount = 0u;
-    ctl->nC = 0u;
-    ctl->sig_out = 0ull;
-    ctl->cmd = 0;
-  }
-  grid.sync();
+  // A resuming launch runs only after a launch that stopped for an external
+  // refresh (the same word in every thread: the previous launch wrote it).
+  if (a.resume && __ldcg(&ctl->ext_state) != 1) return;
 
   Driver d;
   bool bounded = false;
@@ -89,8 +84,68 @@ __global__ void __launch_bounds__(kCelfThreads, 1) k_celf(CelfArgs a) {
   uint32_t pass_id = 0, extracts = 0, refreshes = 0;
   int cmd = kCmdExtract;
   uint32_t outer = 0;
+  if (!a.resume) {
+    for (uint32_t i = gtid; i < 3 * kBins; i += gthreads) (&ctl->hist[0][0])[i] = 0u;
+    for (uint32_t i = gtid; i < a.n; i += gthreads) a.chosen[i] = 0;
+    if (gtid == 0) {
+      ctl->kmin = ~0ull;
+      ctl->kmax = 0ull;
+      ctl->kcount = 0u;
+      ctl->nC = 0u;
+      ctl->sig_out = 0ull;
+      ctl->cmd = 0;
+      ctl->ext_state = 0;
+    }
+  } else {  // the state left by the stopped launch; the keys are refreshed
+    d.nsel = __ldcg(&ctl->s_nsel);
+    d.sigma = __ldcg(&ctl->s_sigma);
+    d.rounds = __ldcg(&ctl->s_rounds);
+    d.evals = __ldcg(&ctl->s_evals);
+    d.lb = __ldcg(&ctl->s_lb);
+    for (int i = 0; i < 4; ++i) d.cyc[i] = __ldcg(&ctl->s_cyc[i]);
+    for (int i = 0; i < 2; ++i) d.fine[i] = __ldcg(&ctl->s_fine[i]);
+    outer = __ldcg(&ctl->s_outer);
+    extracts = __ldcg(&ctl->s_extracts);
+    refreshes = __ldcg(&ctl->s_refreshes) + 1;
+    pass_id = __ldcg(&ctl->s_pass);
+    A0 = __ldcg(&ctl->kmin);
+    B0 = __ldcg(&ctl->kmax);
+  }
+  grid.sync();
+  if (a.resume && gtid == 0) {  // every thread has read the state
+    ctl->ext_state = 0;
+    ctl->kmin = ~0ull;
+    ctl->kmax = 0ull;
+    ctl->kcount = 0u;
+  }
+
+  bool stopped = false;
   for (; outer < a.round_cap; ++outer) {
     const long long t0 = clock64();
+    if (cmd == kCmdRefresh && a.ext_left > 0) {
+      // Stop for the refresh kernel queued behind this launch: the driver's
+      // state goes to the control block, the key statistics start empty.
+      if (gtid == 0) {
+        ctl->s_nsel = d.nsel;
+        ctl->s_sigma = d.sigma;
+        ctl->s_rounds = d.rounds;
+        ctl->s_evals = d.evals;
+        ctl->s_lb = d.lb;
+        for (int i = 0; i < 4; ++i) ctl->s_cyc[i] = d.cyc[i];
+        for (int i = 0; i < 2; ++i) ctl->s_fine[i] = d.fine[i];
+        ctl->s_outer = outer;
+        ctl->s_extracts = extracts;
+        ctl->s_refreshes = refreshes;
+        ctl->s_pass = pass_id;
+        ctl->kmin = ~0ull;
+        ctl->kmax = 0ull;
+        ctl->kcount = 0u;
+        __threadfence();
+        ctl->ext_state = 1;
+      }
+      stopped = true;
+      break;
+    }
     if (cmd == kCmdRefresh) {
       grid_refresh(a, __ldcg(&ctl->refresh_lb));
       grid.sync();
@@ -198,6 +253,7 @@ __global__ void __launch_bounds__(kCelfThreads, 1) k_celf(CelfArgs a) {
     cmd = __ldcg(&ctl->cmd);
     if (cmd == kCmdDone || cmd == kCmdFail) break;
   }
+  if (stopped) return;  // the resuming launch reports the counters
   if (outer >= a.round_cap && gtid == 0) set_status(a.status, IM_ETIMEOUT);
   if (driver && tid == 0 && a.stats) {
     atomicAdd(a.stats + 0, (unsigned long long)d.rounds);
@@ -210,46 +266,83 @@ __global__ void __launch_bounds__(kCelfThreads, 1) k_celf(CelfArgs a) {
   }
 }
 
-cudaError_t launch_celf(const im_graph *g, const im_workspace *ws, const QueryParams &q, int K,
-                        int32_t *d_seeds, uint64_t *d_sigma, cudaStream_t s) {
-  if (K <= 0) return cudaSuccess;
-  CelfArgs a;
-  a.P = ws->d_P;
-  a.cov = ws->d_cov;
-  a.keys = ws->d_keys;
-  a.keyrange = ws->d_keyrange;
-  a.chosen = ws->d_chosen;
-  a.ctl = reinterpret_cast<CelfCtl *>(ws->d_celf_ctl);
-  a.n = (uint32_t)g->n;
-  a.R = q.R;
-  a.K = K;
-  a.B = celf_pool_size(q.R);
-  a.pool_smem = celf_pool_in_smem(q.R) ? 1 : 0;
-  // Refresh after 8 exact evaluations without a commit (one pool round that
-  // committed nothing): the refresh re-evaluates only the vertices whose bound
-  // reaches the best exact gain already known, so it is cheap next to a run
-  // of pool rounds. Swept over {8, 16, 32, 64, 128, 256, 1024, 4096, 16384}
-  // and the earlier max(n/64, 4B) on every workload: 8 was never slower and
-  // up to 1.3x faster than 64, which was 1.2-5x faster than the rest (the
-  // 4M-vertex graph: 34.6 -> 6.9 ms), with identical seeds throughout.
-  uint32_t ra = 8;
-  const int64_t ra_ovr = override_value(IM_OVR_CELF_REFRESH_AFTER);
-  if (ra_ovr > 0) ra = ra_ovr < (int64_t)UINT32_MAX ? (uint32_t)ra_ovr : UINT32_MAX;
-  a.refresh_after = ra;
-  a.magic_R = q.R == 1 ? 0u : (uint32_t)(((1ull << 32) + q.R - 1) / q.R);
-  // Every round evaluates at least one candidate, fewer than refresh_after
-  // evaluations separate two commits or a commit and a refresh, and the
-  // round after a refresh commits (its keys are exact); every grid step is
-  // followed by at least one round.
-  a.round_cap = (uint32_t)(K + 2) * (ra + 8) + 1024;
-  const int64_t rc_ovr = override_value(IM_OVR_CELF_ROUND_CAP);
-  if (rc_ovr > 0 && (uint64_t)rc_ovr < a.round_cap) a.round_cap = (uint32_t)rc_ovr;
-  a.g_pool = ws->d_pool;
-  a.out_seeds = d_seeds;
-  a.out_sigma = d_sigma;
-  a.status = ws->d_status;
-  a.stats = ws->d_stats;
-  const size_t dyn = a.pool_smem ? (size_t)2 * a.B * q.R * sizeof(uint32_t) : 0;
+// The refresh as a streaming launch of its own, between a launch that stopped
+// for it and the one that resumes (the same result as grid_refresh): a warp
+// takes 32 vertices (one flag and key per lane), and every one whose bound
+// reaches the driver's lb is re-evaluated against the current seed set with
+// lane j on thread j mod 32, eight slots per thread in flight (consecutive
+// lanes keep the gathers of a shared root in one request; 16-byte row loads
+// measured slower, 8.0 vs 5.4 ms for the lazy greedy on the 4M-vertex graph).
+// Chosen vertices get 0; the key range and count of the valid keys go to the
+// control block. Inside the cooperative lazy-greedy launch the same pass runs
+// at one 1024-thread block per SM (6.9 ms there); on its own it gets eight
+// 256-thread blocks per SM.
+__global__ void __launch_bounds__(256, 8) k_celf_refresh(CelfArgs a) {
+  CelfCtl *ctl = a.ctl;
+  if (__ldcg(&ctl->ext_state) != 1) return;
+  const uint32_t lb = __ldcg(&ctl->refresh_lb);
+  const int lane = threadIdx.x & 31;
+  const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+  const uint32_t R = a.R;
+  uint64_t mn = ~0ull, mx = 0ull;
+  uint32_t c = 0, evaluated = 0;
+  // a warp takes 32 vertices at a time: one flag and one key per lane, then
+  // the qualifying vertices one after another, each row read at once
+  for (uint32_t base = gwarp * 32; base < a.n; base += nwarps * 32) {
+    const uint32_t v0 = base + lane;
+    uint64_t key = 0;
+    bool eval = false;
+    if (v0 < a.n && !__ldcg(a.chosen + v0)) {
+      key = __ldcg(a.keys + v0);
+      eval = (uint32_t)(key >> 32) >= lb;
+    }
+    unsigned todo = __ballot_sync(kFull, eval);
+    while (todo) {
+      const int src = __ffs(todo) - 1;
+      todo &= todo - 1;
+      const uint32_t v = base + (uint32_t)src;
+      const int32_t *row = a.P + (size_t)v * R;
+      uint32_t g = 0;
+      auto slot = [&](int32_t x, uint32_t j) {
+        const uint32_t root = x < 0 ? v : (uint32_t)x;
+        const uint32_t sz = x < 0 ? (uint32_t)(-x) : (uint32_t)(-__ldg(a.P + (size_t)x * R + j));
+        const uint32_t bit = root * R + j;
+        const uint32_t cw = (x != -1) ? __ldcg(a.cov + (bit >> 5)) : 0u;
+        return ((cw >> (bit & 31)) & 1u) ? 0u : sz;
+      };
+#pragma unroll 8
+      for (uint32_t j = lane; j < R; j += 32) g += slot(__ldg(row + j), j);
+#pragma unroll
+      for (int d = 16; d > 0; d >>= 1) g += __shfl_xor_sync(kFull, g, d);
+      if (lane == src) key = make_key(g, (int32_t)v);
+      ++evaluated;
+    }
+    if (v0 < a.n) {
+      if (eval || key == 0) a.keys[v0] = key;  // chosen vertices get 0
+      if (key) {
+        mn = umin64(mn, key);
+        mx = umax64(mx, key);
+        ++c;
+      }
+    }
+  }
+  mn = warp_min_u64(mn);
+  mx = warp_max_u64(mx);
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) c += __shfl_xor_sync(kFull, c, d);
+  if (lane == 0 && c) {
+    atomicMin(&ctl->kmin, (unsigned long long)mn);
+    atomicMax(&ctl->kmax, (unsigned long long)mx);
+    atomicAdd(&ctl->kcount, c);
+  }
+  if (lane == 0 && evaluated && a.stats)
+    atomicAdd(a.stats + IM_STAT_CELF_REFRESHED, (unsigned long long)evaluated);
+}
+
+// One cooperative lazy-greedy launch with arguments a.
+static cudaError_t launch_celf_once(const im_graph *g, CelfArgs a, cudaStream_t s) {
+  const size_t dyn = a.pool_smem ? (size_t)2 * a.B * a.R * sizeof(uint32_t) : 0;
   const void *fn = a.pool_smem ? (const void *)k_celf<true> : (const void *)k_celf<false>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)kPoolSmemBudget);
@@ -299,6 +392,81 @@ cudaError_t launch_celf(const im_graph *g, const im_workspace *ws, const QueryPa
   if (nclusters > max_clusters) nclusters = max_clusters;
   cfg.gridDim = dim3((unsigned)(nclusters * csize));
   return cudaLaunchKernelExC(&cfg, fn, args);
+}
+
+cudaError_t launch_celf(const im_graph *g, const im_workspace *ws, const QueryParams &q, int K,
+                        int32_t *d_seeds, uint64_t *d_sigma, cudaStream_t s) {
+  if (K <= 0) return cudaSuccess;
+  CelfArgs a;
+  a.P = ws->d_P;
+  a.cov = ws->d_cov;
+  a.keys = ws->d_keys;
+  a.keyrange = ws->d_keyrange;
+  a.chosen = ws->d_chosen;
+  a.ctl = reinterpret_cast<CelfCtl *>(ws->d_celf_ctl);
+  a.n = (uint32_t)g->n;
+  a.R = q.R;
+  a.K = K;
+  a.B = celf_pool_size(q.R);
+  a.pool_smem = celf_pool_in_smem(q.R) ? 1 : 0;
+  // Refresh after 8 exact evaluations without a commit (one pool round that
+  // committed nothing): the refresh re-evaluates only the vertices whose bound
+  // reaches the best exact gain already known, so it is cheap next to a run
+  // of pool rounds. Swept over {8, 16, 32, 64, 128, 256, 1024, 4096, 16384}
+  // and the earlier max(n/64, 4B) on every workload: 8 was never slower and
+  // up to 1.3x faster than 64, which was 1.2-5x faster than the rest (the
+  // 4M-vertex graph: 34.6 -> 6.9 ms), with identical seeds throughout.
+  uint32_t ra = 8;
+  const int64_t ra_ovr = override_value(IM_OVR_CELF_REFRESH_AFTER);
+  if (ra_ovr > 0) ra = ra_ovr < (int64_t)UINT32_MAX ? (uint32_t)ra_ovr : UINT32_MAX;
+  a.refresh_after = ra;
+  a.magic_R = q.R == 1 ? 0u : (uint32_t)(((1ull << 32) + q.R - 1) / q.R);
+  // Every round evaluates at least one candidate, fewer than refresh_after
+  // evaluations separate two commits or a commit and a refresh, and the
+  // round after a refresh commits (its keys are exact); every grid step is
+  // followed by at least one round.
+  a.round_cap = (uint32_t)(K + 2) * (ra + 8) + 1024;
+  const int64_t rc_ovr = override_value(IM_OVR_CELF_ROUND_CAP);
+  if (rc_ovr > 0 && (uint64_t)rc_ovr < a.round_cap) a.round_cap = (uint32_t)rc_ovr;
+  a.g_pool = ws->d_pool;
+  a.out_seeds = d_seeds;
+  a.out_sigma = d_sigma;
+  a.status = ws->d_status;
+  a.stats = ws->d_stats;
+  a.resume = 0;
+  a.ext_left = 0;
+  // Large graphs: the bulk refresh runs as a streaming launch of its own
+  // (k_celf_refresh) between a lazy-greedy launch that stops for it and one
+  // that resumes; two such pairs are queued (each returns at once unless the
+  // launch before it stopped), and any later refresh runs inside the launch.
+  int ext = (uint32_t)g->n > kExtRefreshMinN ? 1 : 0;
+  const int64_t x_ovr = override_value(IM_OVR_CELF_EXT_REFRESH);
+  if (x_ovr == 1) ext = 1;
+  if (x_ovr == 2) ext = 0;
+  if (!ext) return launch_celf_once(g, a, s);
+  constexpr int kExtPairs = 2;
+  const void *rfn = (const void *)k_celf_refresh;
+  int rper_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&rper_sm, rfn, 256, 0);
+  if (e != cudaSuccess) return e;
+  if (rper_sm < 1) rper_sm = 1;
+  uint64_t rblocks = ((uint64_t)g->n + 255) / 256;  // a warp per 32 vertices
+  if (rblocks > (uint64_t)g->num_sms * rper_sm) rblocks = (uint64_t)g->num_sms * rper_sm;
+  a.ext_left = kExtPairs;
+  e = launch_celf_once(g, a, s);
+  for (int k = 0; k < kExtPairs && e == cudaSuccess; ++k) {
+    {
+      void *rargs[] = {&a};
+      e = cudaLaunchKernel(rfn, dim3((unsigned)rblocks), dim3(256), rargs, 0, s);
+    }
+    if (e != cudaSuccess) break;
+    api_count_launch();
+    a.resume = 1;
+    a.ext_left = kExtPairs - 1 - k;
+    e = launch_celf_once(g, a, s);
+    if (e == cudaSuccess) api_count_launch();
+  }
+  return e;
 }
 
 }  // namespace imgb

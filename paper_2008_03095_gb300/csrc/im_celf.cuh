@@ -53,6 +53,13 @@ struct CelfCtl {
   unsigned int refresh_lb;  // driver -> grid: the refresh bound (see grid_refresh)
   unsigned int hist[3][kBins];
   unsigned long long C[kCap];
+  // A launch that stops for an external refresh (large graphs; see
+  // launch_celf) leaves its state here for the launch that resumes.
+  int ext_state;  // 1: stopped for a refresh, not yet resumed
+  int s_nsel;
+  unsigned long long s_sigma;
+  unsigned int s_rounds, s_evals, s_lb, s_outer, s_extracts, s_refreshes, s_pass;
+  unsigned long long s_cyc[4], s_fine[2];
 };
 
 
@@ -77,6 +84,8 @@ struct CelfArgs {
   uint64_t *out_sigma;
   int32_t *status;
   unsigned long long *stats;
+  int resume;    // continue a launch that stopped for an external refresh (else return)
+  int ext_left;  // external refreshes this launch may stop for (0: refresh in the launch)
 };
 
 struct CelfSmem {

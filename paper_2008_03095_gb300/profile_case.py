@@ -8,8 +8,10 @@ a fixed seed set (k_prep, k_spread through im_estimate_spread), each
 
 The seed set of the spread is the K highest-degree vertices (lowest id first
 on equal degree), or with `--selected-seeds` the seeds that im_select_seeds
-picks (selected once, before the profiled runs). Prints one JSON line with
-the per-phase event times.
+picks (selected once, before the profiled runs). `--select` profiles whole
+selections instead (the lazy greedy included); `--ext-refresh 1|2` forces the
+lazy greedy's bulk refresh into a launch of its own or inside the launch.
+Prints one JSON line with the per-phase event times.
 """
 import argparse
 import json
@@ -32,6 +34,9 @@ def main(argv=None):
     ap.add_argument("--R", type=int, default=None)
     ap.add_argument("--selected-seeds", action="store_true",
                     help="spread the seeds im_select_seeds picks instead of the top-degree ones")
+    ap.add_argument("--select", action="store_true", help="profile whole selections")
+    ap.add_argument("--ext-refresh", type=int, default=0,
+                    help="1: the bulk refresh as a launch of its own; 2: inside the launch")
     args = ap.parse_args(argv)
 
     sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
@@ -56,6 +61,8 @@ def main(argv=None):
     seeds = np.argsort(-deg, kind="stable")[:K].astype(np.int32)
     torch.cuda.set_device(0)
     g = im.im_graph_create(xadj, adj)
+    if args.ext_refresh:
+        im.im_debug_override(im.IM_OVR_CELF_EXT_REFRESH, args.ext_refresh)
     if args.selected_seeds:
         seeds, _ = im.im_select_seeds(g, K, R, p, seed)
         seeds = np.ascontiguousarray(seeds, dtype=np.int32)
@@ -69,6 +76,9 @@ def main(argv=None):
     for _ in range(args.repeat):
         if args.spread_only:
             im.im_estimate_spread_async(g, ws, d_seeds, K, R, p, seed, d_sigma)
+            continue
+        if args.select:
+            im.im_select_seeds(g, K, R, p, seed)
             continue
         mg = im.im_debug_first_gains(g, R, p, seed)
         if not args.no_spread:

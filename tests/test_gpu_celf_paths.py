@@ -10,6 +10,11 @@ prefix-extraction paths, against the oracle's naive greedy.
   values of p, with the work counters showing that prefixes were extracted.
 - First-seed gains: mg_v = sum_r |C_r(v)| of every vertex equals the oracle's
   marginal gains for the empty seed set (Algorithm 5, final loop).
+- External bulk refresh (by default above 2^20 vertices, forced here): the
+  launch stops for the refresh, a streaming launch refreshes the bounds and a
+  second launch resumes (refreshes beyond the two queued pairs run inside the
+  launch, as without the option). The seeds and sigma*R equal the oracle's,
+  at the default refresh threshold and at one evaluation.
 """
 import numpy as np
 import pytest
@@ -123,3 +128,30 @@ def test_first_seed_gains_equal_oracle_marginal_gains(name, mk, R, p):
     got = im.im_debug_first_gains(g, R, p, 7)
     g.close()
     assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("refresh_after,shape", [(0, 0), (1, 0), (1, -1)])
+@pytest.mark.parametrize("case", ["local_extraction", "grid_extraction"])
+def test_external_refresh_matches_oracle(clear_overrides, graph_100k, case, refresh_after, shape):
+    if case == "local_extraction":
+        xadj, adj = synth.chung_lu(3000, 15000, 2.2, 11)
+        K, R, p = 25, 256, 0.05
+    else:
+        xadj, adj = graph_100k
+        K, R, p = 50, 256, 0.05
+    oseeds, osigma = oracle.select_seeds(xadj, adj, K, R, p, 7)
+    g = im.im_graph_create(xadj, adj)
+    try:
+        im.im_debug_override(im.IM_OVR_CELF_EXT_REFRESH, 1)
+        im.im_debug_override(im.IM_OVR_CELF_REFRESH_AFTER, refresh_after)
+        im.im_debug_override(im.IM_OVR_CELF_CLUSTER, shape)
+        seeds, sigma, stats = _select_async(g, K, R, p, 7)
+        assert stats["check_code"] == 0, stats
+        assert np.array_equal(seeds, oseeds) and np.array_equal(sigma, osigma)
+        assert stats["celf_refreshes"] >= 1, stats
+        im.im_debug_override(im.IM_OVR_CELF_EXT_REFRESH, 2)  # the refresh inside the launch
+        s2, g2, st2 = _select_async(g, K, R, p, 7)
+        assert st2["celf_refreshes"] == stats["celf_refreshes"]
+        assert np.array_equal(s2, oseeds) and np.array_equal(g2, osigma)
+    finally:
+        g.close()
