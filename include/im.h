@@ -372,7 +372,9 @@ enum {
                                      than L2 with n R < 112 m) */
   IM_STAT_MEMO_ACCUMULATORS = 17, /* size memos run with per-warp root-count accumulators (a
                                      sampled component held more than 4.5% of the vertices) */
-  IM_NUM_STATS = 18
+  IM_STAT_MEMO_LIVE = 18,         /* ... of those, walking only the listed non-root slots (fewer
+                                     than 15% of the sampled slots were non-roots) */
+  IM_NUM_STATS = 19
 };
 /* out: host array of IM_NUM_STATS int64 values. */
 int im_workspace_stats(im_workspace *ws, int64_t *out);

@@ -322,7 +322,7 @@ STATS = ("celf_rounds", "celf_evaluations", "celf_extractions", "spread_levels",
          "celf_cycles_extract", "celf_cycles_eval", "celf_cycles_commit", "celf_cycles_merge",
          "celf_refreshes", "celf_cycles_commits", "celf_cycles_cover", "celf_refreshed",
          "celf_cycles_refresh", "check_code", "check_v0", "check_v1", "spread_components",
-         "memo_accumulators")
+         "memo_accumulators", "memo_live")
 
 
 def im_workspace_stats(ws):

@@ -269,14 +269,14 @@ int ws_create(const im_graph *g, int32_t R_max, im_workspace **out) {
   WS_ALLOC(d_Q2, n + (size_t)g->m / 16 + 1);
   WS_ALLOC(d_inlist, n);
   WS_ALLOC(d_cnt, 2 * (n + 4));
-  WS_ALLOC(d_acc, 6);  // spread: sigma, hand-over word, block counter; size-memo probe: 3
+  WS_ALLOC(d_acc, 7);  // spread: sigma, hand-over word, block counter; size-memo probe: 4
   WS_ALLOC(d_stats, IM_NUM_STATS);
   WS_ALLOC(d_status, 1);
   WS_ALLOC(d_seeds_out, n);
   WS_ALLOC(d_sigma_out, n);
 #undef WS_ALLOC
   if (e == cudaSuccess) e = cudaMemset(ws->d_status, 0, sizeof(int32_t));
-  if (e == cudaSuccess) e = cudaMemset(ws->d_acc, 0, 6 * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMemset(ws->d_acc, 0, 7 * sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMemset(ws->d_stats, 0, sizeof(unsigned long long) * IM_NUM_STATS);
   if (e != cudaSuccess) {
     ws_free(ws);

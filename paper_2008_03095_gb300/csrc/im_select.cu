@@ -164,9 +164,15 @@ cudaError_t launch_union(const im_graph *g, const im_workspace *ws, const QueryP
 // kProbeVertices vertices (a multiplicative hash of the index) are walked to
 // their roots and the most frequent root's count is summed; the last block
 // writes the choice. 16 x 256 samples put the estimate within about 0.3% of
-// the share near the threshold.
+// the share near the threshold. The probe also counts the sampled slots that
+// are not roots: below kMemoLiveShare of them, the accumulator walk lists a
+// warp's few non-root slots and walks only those (4M-vertex graph, 10% of
+// slots: 6.73 vs 7.60 ms); above it the list takes several passes and the
+// walk over all four items of a thread is faster (the 37k-vertex graph at
+// p = 0.05, 27%: 323 vs 373 µs).
 constexpr uint32_t kProbeLanes = 16, kProbeVertices = 256;
-constexpr double kMemoAccShare = 0.045;
+constexpr double kMemoAccShare = 0.045, kMemoLiveShare = 0.15;
+enum : unsigned long long { kMemoPlain = 0, kMemoAcc = 1, kMemoNone = 2, kMemoAccLive = 3 };
 
 __global__ void __launch_bounds__(kProbeVertices) k_memo_probe(const int32_t *P, uint32_t n,
                                                                uint32_t R, uint32_t cap,
@@ -174,19 +180,20 @@ __global__ void __launch_bounds__(kProbeVertices) k_memo_probe(const int32_t *P,
                                                                unsigned long long *probe,
                                                                unsigned long long *stats,
                                                                const unsigned long long *gate) {
-  // probe[0]: the choice (1 = accumulators, 0 = path compression, 2 = no size
-  // memo: the gate is closed); [1]: summed mode counts; [2]: blocks done
+  // probe[0]: the choice (kMemo*; kMemoNone when the gate is closed);
+  // [1]: summed mode counts; [2]: blocks done; [3]: non-root samples
   __shared__ uint32_t s_root[kProbeVertices];
-  __shared__ uint32_t s_max[kProbeVertices / 32];
+  __shared__ uint32_t s_max[kProbeVertices / 32], s_nr[kProbeVertices / 32];
   __shared__ bool s_last;
   if (gate && __ldcg(gate) == 0ull) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) probe[0] = 2ull;
+    if (blockIdx.x == 0 && threadIdx.x == 0) probe[0] = kMemoNone;
     return;
   }
   const uint32_t j = (uint32_t)(((uint64_t)blockIdx.x * R) / gridDim.x);
   const uint32_t v = (uint32_t)(((uint64_t)threadIdx.x * 2654435761u + blockIdx.x) % n);
   uint32_t r = v;
   int32_t x = __ldcg(P + (uint64_t)v * R + j);
+  const unsigned nr = __ballot_sync(kFull, x >= 0);
   for (uint32_t it = 0; x >= 0; ++it) {
     if (it >= cap) {
       set_status(status, IM_ETIMEOUT);
@@ -204,33 +211,45 @@ __global__ void __launch_bounds__(kProbeVertices) k_memo_probe(const int32_t *P,
     const uint32_t o = __shfl_xor_sync(kFull, c, d);
     c = o > c ? o : c;
   }
-  if ((threadIdx.x & 31) == 0) s_max[threadIdx.x >> 5] = c;
+  if ((threadIdx.x & 31) == 0) {
+    s_max[threadIdx.x >> 5] = c;
+    s_nr[threadIdx.x >> 5] = (uint32_t)__popc(nr);
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
-    uint32_t m = 0;
-    for (uint32_t w = 0; w < kProbeVertices / 32; ++w) m = s_max[w] > m ? s_max[w] : m;
+    uint32_t m = 0, nrs = 0;
+    for (uint32_t w = 0; w < kProbeVertices / 32; ++w) {
+      m = s_max[w] > m ? s_max[w] : m;
+      nrs += s_nr[w];
+    }
     atomicAdd(probe + 1, (unsigned long long)m);
+    atomicAdd(probe + 3, (unsigned long long)nrs);
     __threadfence();
     s_last = atomicAdd(probe + 2, 1ull) == gridDim.x - 1;
   }
   __syncthreads();
   if (s_last && threadIdx.x == 0) {
     __threadfence();
-    const double share = (double)__ldcg(probe + 1) / ((double)gridDim.x * kProbeVertices);
-    probe[0] = share > kMemoAccShare ? 1ull : 0ull;
-    if (probe[0] && stats) atomicAdd(stats + IM_STAT_MEMO_ACCUMULATORS, 1ull);
+    const double samples = (double)gridDim.x * kProbeVertices;
+    const double share = (double)__ldcg(probe + 1) / samples;
+    const double nonroot = (double)__ldcg(probe + 3) / samples;
+    probe[0] = share > kMemoAccShare ? (nonroot < kMemoLiveShare ? kMemoAccLive : kMemoAcc)
+                                     : kMemoPlain;
+    if (probe[0] != kMemoPlain && stats) atomicAdd(stats + IM_STAT_MEMO_ACCUMULATORS, 1ull);
+    if (probe[0] == kMemoAccLive && stats) atomicAdd(stats + IM_STAT_MEMO_LIVE, 1ull);
     probe[1] = 0ull;
     probe[2] = 0ull;
+    probe[3] = 0ull;
   }
 }
 
 // Eight blocks per SM (32 registers): measured faster than six or three
-// blocks with more registers. Both instances are queued; the one *mode (from
-// k_memo_probe: 1 accumulators, 0 path compression) does not pick returns at once (holding both walks in one
-// kernel, behind a run-time branch or as two non-inlined loops, compiled the
-// accumulator walk 3-45% slower). Tile t covers vertices 32 (t / tl) ..,
+// blocks with more registers. The three instances are queued; the two that
+// *mode (from k_memo_probe) does not pick return at once (holding the walks
+// in one kernel, behind a run-time branch or as non-inlined loops, compiled
+// the accumulator walk 3-45% slower). Tile t covers vertices 32 (t / tl) ..,
 // lanes 32 (t % tl) ..; n R < 2^32 keeps the tile count within 32 bits.
-template <bool ACC>
+template <bool ACC, bool LIVE = false>
 __global__ void __launch_bounds__(256, 8) k_compress(int32_t *P, uint32_t n, uint32_t R,
                                                      int32_t *status, uint32_t cap,
                                                      const unsigned long long *mode) {
@@ -239,7 +258,7 @@ __global__ void __launch_bounds__(256, 8) k_compress(int32_t *P, uint32_t n, uin
   const uint32_t tl = (R + kCompL - 1) / kCompL;
   const uint32_t ntiles = (n + kCompV - 1) / kCompV * tl;
   uint32_t t = blockIdx.x;
-  if (t >= ntiles || __ldcg(mode) != (ACC ? 1ull : 0ull)) return;
+  if (t >= ntiles || __ldcg(mode) != (ACC ? (LIVE ? kMemoAccLive : kMemoAcc) : kMemoPlain)) return;
   const uint32_t gq = gridDim.x / tl, gr = gridDim.x % tl;  // the grid stride in tiles
   uint32_t tv = t / tl, tj = t % tl;
   // The next tile's rows are loaded while the current tile's chains are
@@ -265,7 +284,11 @@ __global__ void __launch_bounds__(256, 8) k_compress(int32_t *P, uint32_t n, uin
         root_acc_flush(P, R, acc_tj * kCompL, threadIdx.x, acc);
         acc_tj = tj;
       }
-      compress_walk_acc<0>(P, R, status, cap, tv * kCompV, tj * kCompL, tile, threadIdx.x, acc);
+      if (LIVE)
+        compress_walk_acc_live<0>(P, R, status, cap, tv * kCompV, tj * kCompL, tile, threadIdx.x,
+                                  acc);
+      else
+        compress_walk_acc<0>(P, R, status, cap, tv * kCompV, tj * kCompL, tile, threadIdx.x, acc);
     } else {
       compress_walk<0>(P, R, status, cap, tv * kCompV, tj * kCompL, tile, threadIdx.x);
     }
@@ -292,6 +315,11 @@ cudaError_t launch_compress(const im_graph *g, const im_workspace *ws, const Que
   // root-count accumulators are paid once at the end
   if (blocks > bcap) blocks = bcap >= tl ? bcap / tl * tl : bcap;
   if (blocks == 0) blocks = 1;
+  k_compress<true, true><<<(unsigned)blocks, 256, 0, s>>>(ws->d_P, (uint32_t)g->n, q.R,
+                                                          ws->d_status, cap, probe);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  api_count_launch();
   k_compress<true><<<(unsigned)blocks, 256, 0, s>>>(ws->d_P, (uint32_t)g->n, q.R, ws->d_status,
                                                     cap, probe);
   e = cudaGetLastError();

@@ -291,6 +291,89 @@ static __device__ __forceinline__ void compress_walk_acc(int32_t *P, uint32_t R,
   group_sync<BAR>();  // the tile is restaged next
 }
 
+// The accumulator walk on the tile's live slots only: the warp's four items
+// (lanes w + 8q of the 32 vertices) usually hold few non-root slots, so the
+// warp lists them (a ballot per item), and each thread takes one listed slot
+// (passes of 32), walks it to its root, and the slots are counted by one
+// match over (root, item): into the warp's accumulators where the root is
+// the item's accumulated one, else one atomic per group. Same results as
+// compress_walk_acc; ends with the group's barrier.
+template <int BAR>
+static __device__ __forceinline__ void compress_walk_acc_live(int32_t *P, uint32_t R,
+                                                              int32_t *status, uint32_t cap,
+                                                              uint32_t v0, uint32_t j0,
+                                                              int32_t (*tile)[kCompL + 1],
+                                                              uint32_t tid, RootAcc *acc) {
+  const uint32_t lane = tid & 31u, warp = tid >> 5;
+  unsigned bal[4];
+  uint32_t off[5];
+  off[0] = 0;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    bal[q] = __ballot_sync(kFull, tile[lane][warp + 8u * q] >= 0);
+    off[q + 1] = off[q] + (uint32_t)__popc(bal[q]);
+  }
+  const uint32_t total = off[4];
+  for (uint32_t base = 0; base < total; base += 32) {  // warp-uniform
+    const uint32_t k = base + lane;
+    const bool live0 = k < total;
+    uint32_t q = 0, l = 0;
+    int32_t x = -1;
+    if (live0) {
+      q = k >= off[2] ? (k >= off[3] ? 3u : 2u) : (k >= off[1] ? 1u : 0u);
+      const unsigned bq = q == 0 ? bal[0] : q == 1 ? bal[1] : q == 2 ? bal[2] : bal[3];
+      const uint32_t oq = q == 0 ? off[0] : q == 1 ? off[1] : q == 2 ? off[2] : off[3];
+      l = __fns(bq, 0, (int)(k - oq + 1));  // the (k - oq)-th listed vertex of item q
+      x = tile[l][warp + 8u * q];
+    }
+    const uint32_t j = j0 + warp + 8u * q;
+    int32_t r = x;
+    bool live = live0;
+    for (uint32_t it = 0; live; ++it) {  // r is a non-root vertex of the chain
+      const int32_t z = __ldcg(P + (uint64_t)(uint32_t)r * R + j);
+      if (z < 0) break;
+      r = z;
+      if (it + 1 >= cap) {  // longer than any chain of n vertices: a corrupt table
+        set_status(status, IM_ETIMEOUT);
+        live = false;
+      }
+    }
+    uint32_t ar[4];
+#pragma unroll
+    for (int qq = 0; qq < 4; ++qq) ar[qq] = acc->root[qq];  // every lane reads before lane 0 writes
+    __syncwarp();
+#pragma unroll
+    for (int qq = 0; qq < 4; ++qq) {
+      const uint32_t m = __reduce_min_sync(kFull, (live && q == (uint32_t)qq) ? (uint32_t)r : 0xffffffffu);
+      if (m < ar[qq]) {  // a smaller root: pay the old one, follow the new one
+        if (lane == 0) {
+          if (acc->cnt[qq]) atomicAdd(P + (uint64_t)ar[qq] * R + (j0 + warp + 8u * qq), -acc->cnt[qq]);
+          acc->root[qq] = m;
+          acc->cnt[qq] = 0;
+        }
+        ar[qq] = m;
+      }
+    }
+    const uint32_t arq = q == 0 ? ar[0] : q == 1 ? ar[1] : q == 2 ? ar[2] : ar[3];
+    const bool mine = live && (uint32_t)r == arq;
+#pragma unroll
+    for (int qq = 0; qq < 4; ++qq) {
+      const unsigned mm = __ballot_sync(kFull, mine && q == (uint32_t)qq);
+      if (lane == 0 && mm) acc->cnt[qq] += __popc(mm);
+    }
+    const unsigned long long key =
+        (live && !mine) ? (((unsigned long long)(uint32_t)r << 2) | q) : ~0ull;
+    const unsigned peers = __match_any_sync(kFull, key);
+    if (live) {
+      if (!mine && lane == (uint32_t)(__ffs(peers) - 1))
+        atomicAdd(P + (uint64_t)(uint32_t)r * R + j, -(int32_t)__popc(peers));
+      if (r != x) __stcg(P + (uint64_t)(v0 + l) * R + j, r);
+    }
+    __syncwarp();
+  }
+  group_sync<BAR>();  // the tile is restaged next
+}
+
 // The tile at vertices v0.., lanes j0.., by 256 threads, without
 // accumulators: a thread's four chains are walked one after another, and a
 // chain of two or more links is compressed (its inner vertices get the root

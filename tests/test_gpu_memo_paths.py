@@ -1,7 +1,8 @@
-"""The size memo's two walks (Section 3.3): a one-block-per-lane probe of the
+"""The size memo's walks (Section 3.3): a one-block-per-lane probe of the
 union-find table picks per-warp root-count accumulators where a sample holds
-a large component, and the path-compressing walk otherwise. Both give the
-oracle's tables and seeds; the work counters say which one ran.
+a large component (walking only a warp's listed non-root slots when those are
+few), and the path-compressing walk otherwise. All give the oracle's tables
+and seeds; the work counters say which one ran.
 """
 import numpy as np
 import pytest
@@ -54,6 +55,7 @@ def test_both_walks_equal_oracle(c2, p, accumulate):
     R, K = 1024, 30
     seeds, sigma, st = _select_with_stats(g, K, R, p, 7)
     assert st["memo_accumulators"] == accumulate
+    assert st["memo_live"] == 0  # a quarter of the slots are not roots at p = 0.05
     lab, siz = oracle.labels(xadj, adj, R, p, 7)
     assert np.array_equal(im.im_debug_labels(g, R, p, 7), lab)
     assert np.array_equal(im.im_debug_sizes(g, R, p, 7), siz)
@@ -67,10 +69,28 @@ def test_giant_component_graph_takes_accumulators():
     try:
         R = 64
         seeds, sigma, st = _select_with_stats(g, 10, R, 0.05, 3)
-        assert st["memo_accumulators"] == 1
+        assert st["memo_accumulators"] == 1 and st["memo_live"] == 0
         lanes = np.array([0, 17, 63], dtype=np.int32)
         lab, siz = oracle.labels_lanes(xadj, adj, R, 0.05, 3, lanes)
         glab, gsiz = im.im_debug_tables_lanes(g, R, 0.05, 3, lanes)
         assert np.array_equal(glab, lab) and np.array_equal(gsiz, siz)
+    finally:
+        g.close()
+
+
+def test_few_non_roots_take_the_listed_walk():
+    """A 1M-vertex power-law graph at p = 0.01: its largest component holds
+    about 5% of the vertices, and about 10% of the slots are not roots."""
+    xadj, adj = synth.chung_lu(1_000_000, 8_750_000, 2.2, 42)
+    g = im.im_graph_create(xadj, adj)
+    try:
+        R, p = 64, 0.01
+        seeds, sigma, st = _select_with_stats(g, 10, R, p, 5)
+        assert st["memo_accumulators"] == 1 and st["memo_live"] == 1
+        lanes = np.array([0, 31, 63], dtype=np.int32)
+        lab, siz = oracle.labels_lanes(xadj, adj, R, p, 5, lanes)
+        glab, gsiz = im.im_debug_tables_lanes(g, R, p, 5, lanes)
+        assert np.array_equal(glab, lab) and np.array_equal(gsiz, siz)
+        assert im.im_estimate_spread(g, seeds, R, p, 5) == int(sigma[-1])
     finally:
         g.close()
