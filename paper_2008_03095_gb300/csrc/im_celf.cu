@@ -270,14 +270,15 @@ __global__ void __launch_bounds__(kCelfThreads, 1) k_celf(CelfArgs a) {
 // for it and the one that resumes (the same result as grid_refresh): a warp
 // takes 32 vertices (one flag and key per lane), and every one whose bound
 // reaches the driver's lb is re-evaluated against the current seed set with
-// lane j on thread j mod 32, eight slots per thread in flight (consecutive
-// lanes keep the gathers of a shared root in one request; 16-byte row loads
-// measured slower, 8.0 vs 5.4 ms for the lazy greedy on the 4M-vertex graph).
-// Chosen vertices get 0; the key range and count of the valid keys go to the
-// control block. Inside the cooperative lazy-greedy launch the same pass runs
-// at one 1024-thread block per SM (6.9 ms there); on its own it gets eight
-// 256-thread blocks per SM.
-__global__ void __launch_bounds__(256, 8) k_celf_refresh(CelfArgs a) {
+// lane j on thread j mod 32, sixteen slots per thread in flight (a whole
+// 512-lane row at once; consecutive lanes keep the gathers of a shared root
+// in one request). Measured on the 4M-vertex graph, lazy greedy per
+// selection: 4.97 ms at sixteen slots and four blocks per SM (64 registers),
+// 5.4 ms at eight slots and eight blocks, 5.5 ms at sixteen and six, 8.0 ms
+// with 16-byte row loads, 6.9 ms with the refresh inside the cooperative
+// launch (one 1024-thread block per SM). Chosen vertices get 0; the key range
+// and count of the valid keys go to the control block.
+__global__ void __launch_bounds__(256, 4) k_celf_refresh(CelfArgs a) {
   CelfCtl *ctl = a.ctl;
   if (__ldcg(&ctl->ext_state) != 1) return;
   const uint32_t lb = __ldcg(&ctl->refresh_lb);
@@ -311,7 +312,7 @@ __global__ void __launch_bounds__(256, 8) k_celf_refresh(CelfArgs a) {
         const uint32_t cw = (x != -1) ? __ldcg(a.cov + (bit >> 5)) : 0u;
         return ((cw >> (bit & 31)) & 1u) ? 0u : sz;
       };
-#pragma unroll 8
+#pragma unroll 16
       for (uint32_t j = lane; j < R; j += 32) g += slot(__ldg(row + j), j);
 #pragma unroll
       for (int d = 16; d > 0; d >>= 1) g += __shfl_xor_sync(kFull, g, d);
