@@ -777,8 +777,8 @@ def run_serve(args, pool_graphs):
             try:
                 _, _, times = im.im_server_wait(sv, t)
             except im.IMError as err:  # recorded and re-run alone below
-                failed.append({"index": i, "code": err.code, "query": {k: v for k, v in qs[i].items()
-                                                                        if k != "seeds"}})
+                failed.append({"index": i, "code": err.code, "message": str(err),
+                               "query": {k: v for k, v in qs[i].items() if k != "seeds"}})
                 continue
             lat.append(times[2] - times[0])
             done_t.append(times[2])

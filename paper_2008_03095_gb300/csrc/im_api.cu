@@ -362,9 +362,11 @@ int take_status(const im_workspace *ws, cudaStream_t s) {
   if (st != 0) {
     API_CUDA(cudaMemsetAsync(ws->d_status, 0, sizeof(int32_t), s), "status clear");
     API_CUDA(cudaStreamSynchronize(s), "stream synchronize");
+    if (st == IM_EINTERNAL)
+      return fail(st, "device-side invariant violated: %s", api_check_text(ws, s).c_str());
     const char *what = st == IM_ETIMEOUT ? "a device loop exceeded its iteration budget"
                        : st == IM_EINVAL ? "invalid seed id"
-                                         : "device-side invariant violated";
+                                         : "device-side error";
     return fail(st, "%s", what);
   }
   return IM_OK;
@@ -549,6 +551,26 @@ int fused_sampling_select(im_graph *g, im_workspace *ws, int32_t K, const QueryP
 }  // namespace
 
 namespace imgb {
+
+// The first failed internal invariant check of a query that ended with
+// IM_EINTERNAL (work counters IM_STAT_CHECK_CODE/_V0/_V1), read and cleared
+// on the query's stream, as text for the error message. Code 0 means that the
+// failing step keeps no record (a prefix extraction of the lazy greedy).
+std::string api_check_text(const im_workspace *ws, cudaStream_t s) {
+  unsigned long long v[3] = {0ull, 0ull, 0ull};
+  if (cudaMemcpyAsync(v, ws->d_stats + IM_STAT_CHECK_CODE, sizeof(v), cudaMemcpyDeviceToHost, s) !=
+          cudaSuccess ||
+      cudaMemsetAsync(ws->d_stats + IM_STAT_CHECK_CODE, 0, sizeof(v), s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return "check record unreadable";
+  char buf[160];
+  if (v[0] == 0)
+    std::snprintf(buf, sizeof(buf), "no check record (a prefix extraction step failed)");
+  else
+    std::snprintf(buf, sizeof(buf), "check %llu failed with 0x%llx, 0x%llx", v[0], v[1], v[2]);
+  return buf;
+}
+
 
 int api_error(int code, const char *fmt, ...) {
   char buf[512];

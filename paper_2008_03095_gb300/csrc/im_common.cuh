@@ -7,6 +7,7 @@
 
 #include <cstdint>
 #include <mutex>
+#include <string>
 
 #include "../../include/im.h"
 
@@ -278,6 +279,9 @@ int api_query_params(const im_graph *g, int32_t R, double p, uint32_t seed, uint
 int api_ws_create(const im_graph *g, int32_t R_max, im_workspace **out);
 void api_ws_destroy(im_workspace *ws);
 size_t api_ws_bytes(const im_graph *g, int32_t R_max);  // device bytes of a workspace
+// After a query ended with IM_EINTERNAL: its first failed invariant check as
+// text (read and cleared on s, which is synchronized).
+std::string api_check_text(const im_workspace *ws, cudaStream_t s);
 int api_ws_seed_capacity(im_workspace *ws, int64_t count);
 int api_enqueue_select(const im_graph *g, const im_workspace *ws, int32_t K, const QueryParams &q,
                        int32_t *d_seeds, uint64_t *d_sigma, cudaStream_t s);

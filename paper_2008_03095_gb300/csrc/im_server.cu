@@ -18,6 +18,7 @@
 #include <memory>
 #include <mutex>
 #include <new>
+#include <string>
 #include <thread>
 #include <vector>
 
@@ -39,6 +40,7 @@ struct Request {
   QueryParams q{};
   double t_submit = 0, t_admit = 0, t_done = 0;
   int status = IM_OK;
+  std::string detail;  // failed invariant check of an IM_EINTERNAL result
   bool done = false;
   std::vector<int32_t> out_seeds;
   std::vector<uint64_t> out_sigma;
@@ -93,6 +95,8 @@ void finish(im_server *sv, Slot &sl, int status) {
   std::shared_ptr<Request> r = sl.req;
   const bool select = r->req.kind == IM_REQUEST_SELECT;
   if (status == IM_OK && *sl.h_status != 0) status = *sl.h_status;
+  std::string detail;
+  if (status == IM_EINTERNAL) detail = api_check_text(sl.pw->ws, sl.stream);
   if (status == IM_OK) {
     if (select) {
       r->out_seeds.assign(sl.h_seeds, sl.h_seeds + r->req.K);
@@ -107,6 +111,7 @@ void finish(im_server *sv, Slot &sl, int status) {
   sl.req.reset();
   std::lock_guard<std::mutex> lock(sv->mu);
   r->status = status;
+  r->detail = std::move(detail);
   r->t_done = now_s() - sv->t0;
   r->done = true;
   ++sv->stat[IM_SERVER_STAT_COMPLETED];
@@ -388,7 +393,8 @@ int im_server_wait(im_server *sv, uint64_t ticket, int64_t timeout_us, int32_t *
     out_times[2] = r->t_done;
   }
   if (r->status != IM_OK)
-    return api_error(r->status, "query %llu failed on the device", (unsigned long long)ticket);
+    return api_error(r->status, "query %llu failed on the device%s%s", (unsigned long long)ticket,
+                     r->detail.empty() ? "" : ": ", r->detail.c_str());
   if (r->req.kind == IM_REQUEST_SELECT) {
     if (out_seeds) std::memcpy(out_seeds, r->out_seeds.data(), sizeof(int32_t) * r->out_seeds.size());
     if (out_sigma_R) std::memcpy(out_sigma_R, r->out_sigma.data(), sizeof(uint64_t) * r->out_sigma.size());
