@@ -253,6 +253,10 @@ def run_reference(args, xadj, adj, w):
 # ------------------------------------------------------------------ our arm
 
 
+# Kernel of a profiling phase whose name differs from the phase's.
+KERNEL_OF_PHASE = {"spread_cc": "k_spread_count", "spread_mark": "k_spread_mark"}
+
+
 def algorithmic_bytes(phase, n, m_up, R, T):
     """Minimum bytes one launch of `phase` must move (see the kernel table)."""
     nR = n * R
@@ -262,6 +266,8 @@ def algorithmic_bytes(phase, n, m_up, R, T):
         return 4 * nR  # read every slot once
     if phase == "gains":
         return 4 * nR + 8 * n  # read every slot once, write n keys
+    if phase == "spread_cc":
+        return 4 * nR + nR / 8  # the spread's count: every slot once, its own mark bit
     if phase == "union":
         live = m_up * R * (T / 2.0 ** 32)
         return 8 * m_up + 8 * live  # edge list + both endpoint slots per live arc-lane
@@ -452,13 +458,13 @@ def measure(name, w, xadj, adj, steps, warmup, world, detail):
 
     rec["clocks"] = clock_info
     # Roofline of the dominant kernel (largest share of device time). The
-    # spread's hand-over runs the select path's union and size memo again
-    # (phases spread_union, spread_compress): they count toward those kernels
-    # when every query handed over, so that every launch did the full work.
+    # spread's hand-over runs the select path's union again (phase
+    # spread_union): it counts toward that kernel when every query handed
+    # over, so that every launch did the full work.
     handed_over = all(by_p[str(p)]["per_query"].get("spread_components", 0) >= 1 for p in ps)
     kern = {}
     for ph, (ms, cnt) in prof.items():
-        k = {"spread_union": "union", "spread_compress": "compress"}.get(ph, ph)
+        k = {"spread_union": "union"}.get(ph, ph)
         if k != ph and not handed_over:
             continue
         a, c = kern.get(k, (0.0, 0))
@@ -466,7 +472,8 @@ def measure(name, w, xadj, adj, steps, warmup, world, detail):
     dominant = max(kern, key=lambda k: kern[k][0])
     T = {p: im.im_sampling_threshold(p) for p in ps}
     avg_s = kern[dominant][0] / kern[dominant][1] / 1e3
-    roof = {"kernel": "k_" + dominant, "bound": "hbm", "peak": peak, "unit": "GB/s",
+    roof = {"kernel": KERNEL_OF_PHASE.get(dominant, "k_" + dominant), "bound": "hbm",
+            "peak": peak, "unit": "GB/s",
             "peak_kind": peak_kind, "avg_launch_us": avg_s * 1e6, "launches": kern[dominant][1],
             "share_of_device_time": kern[dominant][0] / tot if tot else None}
     if dominant == "celf":
@@ -493,7 +500,7 @@ def measure(name, w, xadj, adj, steps, warmup, world, detail):
             roof.update(bound="latency", achieved=None, bytes_per_launch=None, traffic=None)
         else:
             roof.update(bytes_per_launch=b, achieved=b / avg_s / 1e9,
-                        traffic=committed_traffic("k_" + dominant, name))
+                        traffic=committed_traffic(roof["kernel"], name))
     if roof.get("achieved") is not None:
         roof["frac"] = roof["achieved"] / peak
         roof["frac_of"] = "measured" if peak_kind == "measured" else "fallback"
@@ -501,12 +508,13 @@ def measure(name, w, xadj, adj, steps, warmup, world, detail):
         roof["frac"] = None
     rec["roofline"] = roof
     hbm = {}
-    for ph in ("prep", "compress", "gains"):
-        if prof[ph][1]:
+    for ph in ("prep", "compress", "gains", "spread_cc"):
+        if prof[ph][1] and (ph != "spread_cc" or handed_over):
             b = algorithmic_bytes(ph, n, 0, R, 0)
             a = b / (prof[ph][0] / prof[ph][1] / 1e3) / 1e9
-            hbm["k_" + ph] = {"achieved_gbs": a, "frac": a / peak, "bytes_per_launch": b,
-                              "traffic": committed_traffic("k_" + ph, name)}
+            kn = KERNEL_OF_PHASE.get(ph, "k_" + ph)
+            hbm[kn] = {"achieved_gbs": a, "frac": a / peak, "bytes_per_launch": b,
+                       "traffic": committed_traffic(kn, name)}
     rec["hbm_kernels"] = hbm
     return rec, (seeds_h, sigma_h, spread_h)
 

@@ -406,12 +406,12 @@ enum {
   IM_PHASE_CELF = 4,         /* on-device lazy greedy */
   IM_PHASE_SPREAD_PREP = 5,  /* X_r draw and lane order for the spread */
   IM_PHASE_SPREAD = 6,       /* bit-parallel multi-source BFS */
-  IM_PHASE_SPREAD_CC = 7,    /* the spread's hand-over to components, last kernel: seed roots
-                                marked and the sizes of the distinct ones summed */
+  IM_PHASE_SPREAD_CC = 7,    /* the spread's hand-over to components, last kernel: the
+                                slots whose root is marked, counted */
   IM_PHASE_SPREAD_UNION = 8, /* ... its union (the select path's kernel) */
-  IM_PHASE_SPREAD_COMPRESS = 9, /* ... its size memo (probe and the select path's kernels); the
-                                   three are queued behind the BFS where a hand-over can pay
-                                   and return at once unless the BFS handed over */
+  IM_PHASE_SPREAD_MARK = 9,  /* ... the seeds' roots marked in every sample; the three are
+                                queued behind the BFS where a hand-over can pay and return
+                                at once unless the BFS handed over */
   IM_NUM_PHASES = 10
 };
 

@@ -346,7 +346,7 @@ def im_sampling_threshold(p):
 
 
 PHASES = ("prep", "union", "compress", "gains", "celf", "spread_prep", "spread", "spread_cc",
-          "spread_union", "spread_compress")
+          "spread_union", "spread_mark")
 
 
 def im_profile_enable(on=True):

@@ -343,12 +343,12 @@ int enqueue_spread(const im_graph *g, const im_workspace *ws, const int32_t *d_s
     API_CUDA(timed(IM_PHASE_SPREAD_UNION, s,
                    [&] { return launch_union(g, ws, qq, d_mask, s, gate); }),
              "k_union (spread)");
-    API_CUDA(timed(IM_PHASE_SPREAD_COMPRESS, s,
-                   [&] { return launch_compress(g, ws, qq, s, gate); }),
-             "k_compress (spread)");
+    API_CUDA(timed(IM_PHASE_SPREAD_MARK, s,
+                   [&] { return launch_spread_mark(g, ws, qq, d_seeds, ns, s); }),
+             "k_spread_mark");
     API_CUDA(timed(IM_PHASE_SPREAD_CC, s,
-                   [&] { return launch_spread_cc(g, ws, qq, d_seeds, ns, d_sigma, s); }),
-             "k_spread_sum");
+                   [&] { return launch_spread_count(g, ws, qq, d_sigma, s); }),
+             "k_spread_count");
   }
   return IM_OK;
 }

@@ -310,14 +310,16 @@ cudaError_t launch_edge_hash(const int32_t *d_u, const int32_t *d_v, int64_t cou
 cudaError_t launch_celf(const im_graph *g, const im_workspace *ws, const QueryParams &q, int K,
                         int32_t *d_seeds, uint64_t *d_sigma, cudaStream_t s);
 // handover: the BFS may hand over (through ws->d_acc[1]): it then initialises
-// the label table and the covered bitmap, and launch_union, launch_compress
-// (both gated by ws->d_acc + 1) and launch_spread_cc must be queued behind it.
+// the label table and the covered bitmap, and launch_union (gated by
+// ws->d_acc + 1), launch_spread_mark and launch_spread_count must be queued
+// behind it, in that order.
 cudaError_t launch_spread(const im_graph *g, const im_workspace *ws, const QueryParams &q,
                           const int32_t *d_seeds, int num_seeds, const uint8_t *d_mask,
                           uint64_t *d_sigma, bool handover, cudaStream_t s);
-cudaError_t launch_spread_cc(const im_graph *g, const im_workspace *ws, const QueryParams &q,
-                             const int32_t *d_seeds, int num_seeds, uint64_t *d_sigma,
-                             cudaStream_t s);
+cudaError_t launch_spread_mark(const im_graph *g, const im_workspace *ws, const QueryParams &q,
+                               const int32_t *d_seeds, int num_seeds, cudaStream_t s);
+cudaError_t launch_spread_count(const im_graph *g, const im_workspace *ws, const QueryParams &q,
+                                uint64_t *d_sigma, cudaStream_t s);
 // FusedSampling variant: single-lane table reset and mg accumulation
 cudaError_t launch_fs_init(const im_graph *g, int32_t *P1, cudaStream_t s);
 cudaError_t launch_fs_accum(const im_graph *g, const int32_t *P1, unsigned long long *mg,

@@ -24,10 +24,10 @@
 // frontier exceeds n/16 vertices (where the BFS's arcs per vertex, times the
 // levels that rescan them, outweigh the R slots per vertex the components
 // cost; the caller decides): the BFS initialises the label table, the
-// components of every sample and their sizes are formed by the select path's
-// union-find and size memo (each edge once, each slot once), and sigmaR sums,
-// in every sample, the sizes of the distinct components holding a seed. The
-// hand-over kernels are queued behind every such BFS and return at once
+// components of every sample are formed by the select path's union-find (each
+// edge once), every (seed, sample) pair marks its root, and sigmaR counts the
+// (vertex, sample) slots whose root is marked (each slot once; no size memo).
+// The hand-over kernels are queued behind every such BFS and return at once
 // unless it handed over, so the choice costs no host round trip.
 #include <cooperative_groups.h>
 
@@ -362,46 +362,109 @@ __global__ void __launch_bounds__(512, 2) k_spread(SpreadArgs a) {
 }
 
 // ------------------------------------------------------------ hand-over path
-struct SpreadSumArgs {
-  const int32_t *P;      // size memo: a root slot holds -|C|, any other slot its root
+// After a hand-over the union's forest is in the label table: a root slot
+// holds -1, any other slot a vertex of its component nearer the root. sigmaR
+// (Eq. 2 summed over the samples) is the number of slots (v, j) whose
+// component holds a seed in sample j: each (seed, sample) pair sets its
+// root's bit in the covered bitmap (cleared by the BFS), then every slot walks
+// to its root and counts itself if that bit is set.
+struct SpreadCountArgs {
+  const int32_t *P;      // the union's forest, n * R slots
   uint32_t n, R;
-  uint32_t *cov;         // marked roots: bit (root R + lane), cleared by the BFS
+  uint32_t *cov;         // bit (root R + lane): the root's component holds a seed
   const int32_t *seeds;
   int num_seeds;
-  unsigned long long *acc, *gate, *done;
+  uint32_t cap;          // walk budget (IM_ETIMEOUT past it)
+  const unsigned long long *gate;
+  unsigned long long *acc, *done;
   uint64_t *out;
+  int32_t *status;
   unsigned long long *stats;
 };
 
-// sigmaR = sum over samples of the sizes of the distinct components holding a
-// seed: every (seed, lane) pair finds its root (one step in the size memo)
-// and marks it; the pair that sets the mark adds the component's size. The
-// last block writes the result.
-__global__ void __launch_bounds__(256) k_spread_sum(SpreadSumArgs a) {
-  __shared__ unsigned long long s_sum[8];
-  __shared__ bool s_last;
+// Root of x in lane j of the forest, read only (the table is not written).
+static __device__ __forceinline__ uint32_t forest_root(const int32_t *__restrict__ P, uint32_t R,
+                                                       uint32_t cap, int32_t *status, uint32_t x,
+                                                       uint32_t j) {
+  for (uint32_t it = 0; it < cap; ++it) {
+    const int32_t y = __ldg(P + x * R + j);
+    if (y < 0) return x;
+    x = (uint32_t)y;
+  }
+  set_status(status, IM_ETIMEOUT);
+  return x;
+}
+
+// Every (seed, lane) pair marks the root of the seed's component.
+__global__ void __launch_bounds__(256) k_spread_mark(SpreadCountArgs a) {
   if (__ldcg(a.gate) == 0ull) return;
   const uint64_t total = (uint64_t)a.num_seeds * a.R;
-  unsigned long long sum = 0;
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
        i += (uint64_t)gridDim.x * blockDim.x) {
     const int32_t s = a.seeds[i / a.R];
     const uint32_t j = (uint32_t)(i % a.R);
     if (s < 0 || (uint32_t)s >= a.n) continue;  // the BFS recorded IM_EINVAL
-    const int32_t x = __ldcg(a.P + (uint64_t)(uint32_t)s * a.R + j);
-    const uint32_t r = x < 0 ? (uint32_t)s : (uint32_t)x;
-    const int32_t sz = x < 0 ? x : __ldcg(a.P + (uint64_t)r * a.R + j);
-    const uint64_t bit = (uint64_t)r * a.R + j;
-    const uint32_t m = 1u << (bit & 31u);
-    if (!(atomicOr(a.cov + (bit >> 5), m) & m)) sum += (unsigned long long)(uint32_t)(-sz);
+    const uint32_t bit = forest_root(a.P, a.R, a.cap, a.status, (uint32_t)s, j) * a.R + j;
+    atomicOr(a.cov + (bit >> 5), 1u << (bit & 31u));
   }
+}
+
+// 1 when slot (v, j), holding x, lies in a marked component.
+static __device__ __forceinline__ uint32_t slot_marked(const int32_t *__restrict__ P,
+                                                       const uint32_t *__restrict__ cov, uint32_t R,
+                                                       uint32_t cap, int32_t *status, int32_t x,
+                                                       uint32_t v, uint32_t j) {
+  const uint32_t bit = (x < 0 ? v : forest_root(P, R, cap, status, (uint32_t)x, j)) * R + j;
+  return (__ldg(cov + (bit >> 5)) >> (bit & 31u)) & 1u;
+}
+
+// A warp per table row (lane-consecutive 16-byte loads, as the first-gains
+// kernel reads it). Four root slots in a row test four consecutive bits of
+// their own row's marks, one word; a non-root slot walks to its root. The
+// last block writes sigmaR.
+__global__ void __launch_bounds__(256, 4) k_spread_count(SpreadCountArgs a) {
+  __shared__ unsigned long long s_sum[8];
+  __shared__ bool s_last;
+  if (__ldcg(a.gate) == 0ull) return;
+  const int lane = threadIdx.x & 31;
+  const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+  const int32_t *__restrict__ P = a.P;
+  const uint32_t *__restrict__ cov = a.cov;
+  const uint32_t R = a.R, n = a.n, cap = a.cap;
+  int32_t *status = a.status;
+  uint32_t cnt = 0;
+  for (uint32_t v = gwarp; v < n; v += nwarps) {
+    const uint32_t base = v * R;
+    if ((R & 3u) == 0) {
+      const int4 *row4 = reinterpret_cast<const int4 *>(P + base);
+#pragma unroll 4
+      for (uint32_t q4 = lane; q4 < (R >> 2); q4 += 32) {
+        const int4 x = __ldg(row4 + q4);
+        const uint32_t j = q4 << 2;
+        if ((x.x & x.y & x.z & x.w) < 0) {  // four roots: bits base + j .. + 3
+          const uint32_t b = base + j;
+          cnt += __popc((__ldg(cov + (b >> 5)) >> (b & 31u)) & 0xfu);
+        } else {
+          cnt += slot_marked(P, cov, R, cap, status, x.x, v, j) +
+                 slot_marked(P, cov, R, cap, status, x.y, v, j + 1) +
+                 slot_marked(P, cov, R, cap, status, x.z, v, j + 2) +
+                 slot_marked(P, cov, R, cap, status, x.w, v, j + 3);
+        }
+      }
+    } else {
+      for (uint32_t j = lane; j < R; j += 32)
+        cnt += slot_marked(P, cov, R, cap, status, __ldg(P + base + j), v, j);
+    }
+  }
+  unsigned long long sum = cnt;
 #pragma unroll
   for (int d = 16; d > 0; d >>= 1) sum += __shfl_xor_sync(kFull, sum, d);
-  if ((threadIdx.x & 31) == 0) s_sum[threadIdx.x >> 5] = sum;
+  if (lane == 0) s_sum[threadIdx.x >> 5] = sum;
   __syncthreads();
   if (threadIdx.x == 0) {
     unsigned long long b = 0;
-    for (int w = 0; w < 8; ++w) b += s_sum[w];
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b += s_sum[w];
     if (b) atomicAdd(a.acc, b);
     __threadfence();
     s_last = atomicAdd(a.done, 1ull) == gridDim.x - 1;
@@ -415,26 +478,47 @@ __global__ void __launch_bounds__(256) k_spread_sum(SpreadSumArgs a) {
   }
 }
 
-cudaError_t launch_spread_cc(const im_graph *g, const im_workspace *ws, const QueryParams &q,
-                             const int32_t *d_seeds, int num_seeds, uint64_t *d_sigma,
-                             cudaStream_t s) {
-  SpreadSumArgs a;
+static SpreadCountArgs count_args(const im_graph *g, const im_workspace *ws, const QueryParams &q,
+                                  const int32_t *d_seeds, int num_seeds, uint64_t *d_sigma) {
+  SpreadCountArgs a;
   a.P = ws->d_P;
   a.n = (uint32_t)g->n;
   a.R = q.R;
   a.cov = ws->d_cov;
   a.seeds = d_seeds;
   a.num_seeds = num_seeds;
-  a.acc = ws->d_acc;
+  a.cap = uf_budget((uint32_t)g->n);
   a.gate = ws->d_acc + 1;
+  a.acc = ws->d_acc;
   a.done = ws->d_acc + 2;
   a.out = d_sigma;
+  a.status = ws->d_status;
   a.stats = ws->d_stats;
+  return a;
+}
+
+cudaError_t launch_spread_mark(const im_graph *g, const im_workspace *ws, const QueryParams &q,
+                               const int32_t *d_seeds, int num_seeds, cudaStream_t s) {
+  const SpreadCountArgs a = count_args(g, ws, q, d_seeds, num_seeds, nullptr);
   const uint64_t pairs = (uint64_t)num_seeds * q.R;
   uint64_t blocks = (pairs + 255) / 256;
   if (blocks > (uint64_t)g->num_sms * 4) blocks = (uint64_t)g->num_sms * 4;
   if (blocks == 0) blocks = 1;
-  k_spread_sum<<<(unsigned)blocks, 256, 0, s>>>(a);
+  k_spread_mark<<<(unsigned)blocks, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_spread_count(const im_graph *g, const im_workspace *ws, const QueryParams &q,
+                                uint64_t *d_sigma, cudaStream_t s) {
+  const SpreadCountArgs a = count_args(g, ws, q, nullptr, 0, d_sigma);
+  int per_sm = 0;
+  const cudaError_t e =
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spread_count, 256, 0);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  uint64_t blocks = ((uint64_t)g->n + 7) / 8;  // a warp per row
+  if (blocks > (uint64_t)g->num_sms * per_sm) blocks = (uint64_t)g->num_sms * per_sm;
+  k_spread_count<<<(unsigned)blocks, 256, 0, s>>>(a);
   return cudaGetLastError();
 }
 

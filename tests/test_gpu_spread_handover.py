@@ -1,6 +1,7 @@
 """The spread's hand-over from the multi-source BFS to the samples' components
 (Algorithm 4 on the fixed samples of Eq. 2; the library switches on tables
-larger than L2 once a BFS frontier passes n/16 vertices): sigma*R equal to
+larger than L2 once a BFS frontier passes n/16 vertices, then marks the
+seeds' roots and counts the slots under a marked root): sigma*R equal to
 the oracle's per-sample BFS with and without the hand-over, under the
 sampling options, with duplicate and empty seed sets, and equal to the lazy
 greedy's sigma*R of its own seeds.
@@ -75,6 +76,18 @@ def test_handover_equals_oracle(torch, giant):
     assert got == oracle.estimate_spread(xadj, adj, seeds, R, p, 7)
     # the blocking call takes the same path
     assert im.im_estimate_spread(g, seeds, R, p, 7) == got
+
+
+def test_handover_lane_count_not_a_multiple_of_four(torch, giant):
+    """The count after the hand-over reads a table row lane by lane when R is
+    not a multiple of 4 (rows are not 16-byte aligned)."""
+    xadj, adj, g = giant
+    R, p = 250, 0.05
+    assert (len(xadj) - 1) * R * 4 > _l2_bytes(torch)
+    seeds = _top_degree(xadj, 12)
+    got, st = _spread(torch, g, seeds, R, p, 13)
+    assert st["spread_components"] == 1
+    assert got == oracle.estimate_spread(xadj, adj, seeds, R, p, 13)
 
 
 @pytest.mark.parametrize("flags", [W, MIX, W | MIX])
