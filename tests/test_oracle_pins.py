@@ -213,6 +213,22 @@ def test_size_table_invariants():
         assert np.array_equal(siz[lab[:, r], r], np.bincount(lab[:, r], minlength=500)[lab[:, r]])
 
 
+def test_bfs_spread_equals_count_of_slots_sharing_a_seed_label():
+    """sigma*R (Algorithm 4's BFS over the samples) equals the number of
+    (vertex, sample) slots whose component label is some seed's label: the
+    identity the spread's hand-over counts on, taken here between two
+    independent oracle routines (BFS and union-find labels)."""
+    xadj, adj = synth.chung_lu(400, 1600, 2.2, 12)
+    R, p, seed = 48, 0.12, 9
+    lab, _ = oracle.labels(xadj, adj, R, p, seed)
+    rng = np.random.default_rng(4)
+    for k in (1, 3, 9):
+        S = rng.choice(400, size=k, replace=False)
+        S = np.concatenate([S, S[:1]])  # a duplicate seed changes nothing
+        count = sum(int(np.isin(lab[:, r], lab[S, r]).sum()) for r in range(R))
+        assert count == oracle.estimate_spread(xadj, adj, [int(x) for x in S], R, p, seed)
+
+
 def test_spread_monotone_and_submodular_exactly():
     xadj, adj = synth.chung_lu(200, 700, 2.4, 31)
     R, p, seed = 64, 0.15, 5
