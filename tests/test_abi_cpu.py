@@ -86,3 +86,36 @@ def test_override_arguments_are_checked(L):
         assert e.value.code == im.IM_EINVAL
     for key in range(im.IM_NUM_OVERRIDES):
         im.im_debug_override(key, 0)
+
+
+def _header_enum(prefix):
+    """{NAME: value} of the `prefix*` enum constants in include/im.h."""
+    import os
+    import re
+    path = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                        "include", "im.h")
+    with open(path) as f:
+        text = f.read()
+    return {m.group(1): int(m.group(2))
+            for m in re.finditer(r"\b(%s[A-Z0-9_]+)\s*=\s*(-?\d+)" % prefix, text)}
+
+
+def test_binding_name_tables_follow_the_header_enums():
+    """The binding's per-phase and per-counter name tables line up with the
+    header's indices, so profiles and work counters are read under the right
+    names."""
+    phases = _header_enum("IM_PHASE_")
+    counts = _header_enum("IM_NUM_")
+    assert len(im.PHASES) == counts["IM_NUM_PHASES"]
+    for name, idx in phases.items():
+        assert im.PHASES[idx] == name[len("IM_PHASE_"):].lower(), name
+    stats = _header_enum("IM_STAT_")
+    assert len(im.STATS) == counts["IM_NUM_STATS"]
+    assert sorted(stats.values()) == list(range(len(im.STATS)))
+    for name in ("IM_STAT_CHECK_CODE", "IM_STAT_SPREAD_COMPONENTS", "IM_STAT_MEMO_LIVE",
+                 "IM_STAT_CELF_ROUNDS", "IM_STAT_CELF_REFRESHED"):
+        assert im.STATS[stats[name]] == name[len("IM_STAT_"):].lower(), name
+    server = _header_enum("IM_SERVER_STAT_")
+    assert len(im.SERVER_STATS) == server.pop("IM_SERVER_STAT_COUNT")
+    for name, idx in server.items():
+        assert im.SERVER_STATS[idx] == name[len("IM_SERVER_STAT_"):].lower(), name
