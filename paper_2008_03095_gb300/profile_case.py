@@ -1,8 +1,9 @@
 """Run the bandwidth kernels of one workload query for a profiler, without the
 lazy greedy: the component pipeline up to the first-seed gains (k_prep,
 k_union, k_compress, k_gains through im_debug_first_gains) and the spread of
-a fixed seed set (k_prep, k_spread through im_estimate_spread), each
-`--repeat` times on one resident graph.
+a fixed seed set (k_prep, k_spread through im_estimate_spread; after a
+hand-over also k_union, k_spread_mark and k_spread_count), each `--repeat`
+times on one resident graph.
 
     python -m paper_2008_03095_gb300.profile_case --workload powerlaw_n37154 --p 0.05
 
